@@ -1,0 +1,166 @@
+"""FP64 CPU oracle for the complex power-of-two DFT (paper Sec. 2.1, Eqs. 1-5).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and
+the benchmark's CPU-baseline / reference arm may import this package.  The
+product path (the CUDA library and ``paper_1707_07263_gb300``) never imports
+it, and the two share no code: this file and ``fft_oracle.c`` hold their own
+arithmetic, written from the paper's definitions.
+
+Functions (all FP64, numpy ``complex128`` in and out):
+
+* ``dft(x, dir)``       -- Eq. 1 (dir 0) / Eq. 2 (dir 1) / adjoint (dir 2),
+                           summed term by term, O(N^2), over the last axis.
+* ``fft(x, dir)``       -- recursive radix-2 decimation in time (the butterfly
+                           of Sec. 2.1), over the last axis.
+* ``fft2(x, dir)``      -- 2-D transform of the last two axes, rows then
+                           columns (Sec. 2.3.2 treats the data as 2-D/3-D and
+                           transforms each dimension in turn).
+* ``spectral_loss(x, w)`` and ``spectral_loss_grad(x, w)`` -- the loss
+  L = sum_k |w_k X_k|^2 with X = Eq. 1 applied to x, and its gradient in
+  PyTorch's convention (dL/dRe + i dL/dIm) = 2 F^H (w^2 * F x), where F^H is
+  the adjoint (conjugate-direction transform without the 1/N, Eq. 4).
+
+Parity of every function here is pinned by ``tests/test_oracle.py`` against
+closed forms, invariants, hand-worked small cases, brute force and an
+independent library routine (numpy's pocketfft).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+FORWARD, INVERSE, ADJOINT = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fft_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``fft_oracle.c`` into ``liboracle.so`` with gcc (plain -O2, no
+    fast-math, so FP64 rounding follows IEEE order)."""
+    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
+             "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load_library(path: str | None = None):
+    """Load the compiled oracle (building it first if needed).  ``path`` lets a
+    test load a deliberately mutated copy."""
+    global _lib
+    if path is None and _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(path or build())
+    i64, vp, ci = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+    for name in ("oracle_dft", "oracle_fft"):
+        fn = getattr(lib, name)
+        fn.argtypes = [i64, vp, vp, ci]
+        fn.restype = ci
+    for name in ("oracle_dft_batch", "oracle_fft_batch"):
+        fn = getattr(lib, name)
+        fn.argtypes = [i64, i64, vp, vp, ci]
+        fn.restype = ci
+    lib.oracle_fft2.argtypes = [i64, i64, vp, vp, ci]
+    lib.oracle_fft2.restype = ci
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _prep(x) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(x), dtype=np.complex128)
+    return a
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _run_batch(name: str, x, dir: int, lib=None) -> np.ndarray:
+    lib = lib or load_library()
+    a = _prep(x)
+    n = a.shape[-1]
+    out = np.empty_like(a)
+    if a.size == 0:
+        return out
+    batch = a.size // n
+    rc = getattr(lib, name)(n, batch, _ptr(a), _ptr(out), dir)
+    if rc != 0:
+        raise ValueError(f"{name}: rejected n={n}, dir={dir} (rc={rc})")
+    return out
+
+
+def dft(x, dir: int = FORWARD, lib=None) -> np.ndarray:
+    """Eq. 1 / Eq. 2 summed directly over the last axis (any N >= 1)."""
+    return _run_batch("oracle_dft_batch", x, dir, lib)
+
+
+def fft(x, dir: int = FORWARD, lib=None) -> np.ndarray:
+    """Recursive radix-2 DIT over the last axis (N a power of two)."""
+    return _run_batch("oracle_fft_batch", x, dir, lib)
+
+
+def fft2(x, dir: int = FORWARD, lib=None) -> np.ndarray:
+    """2-D transform over the last two axes: rows, then columns."""
+    lib = lib or load_library()
+    a = _prep(x)
+    ny, nx = a.shape[-2], a.shape[-1]
+    out = np.empty_like(a)
+    flat_in = a.reshape(-1, ny, nx)
+    flat_out = out.reshape(-1, ny, nx)
+    for i in range(flat_in.shape[0]):
+        src = np.ascontiguousarray(flat_in[i])
+        dst = np.empty_like(src)
+        rc = lib.oracle_fft2(ny, nx, _ptr(src), _ptr(dst), dir)
+        if rc != 0:
+            raise ValueError(f"oracle_fft2: rejected {ny}x{nx} (rc={rc})")
+        flat_out[i] = dst
+    return out
+
+
+def transform(x, dir: int = FORWARD, lib=None) -> np.ndarray:
+    """The oracle's default route: the O(N^2) sum for N <= 1024, the radix-2
+    recursion above that."""
+    n = np.asarray(x).shape[-1]
+    return dft(x, dir, lib) if n <= 1024 else fft(x, dir, lib)
+
+
+def spectral_loss(x, w) -> float:
+    """L = sum_k |w_k * X_k|^2 with X the forward transform (Eq. 1) of x."""
+    X = fft(x, FORWARD)
+    return float(np.sum((np.asarray(w, dtype=np.float64) ** 2) * (X.real ** 2 + X.imag ** 2)))
+
+
+def spectral_loss_grad(x, w) -> np.ndarray:
+    """dL/dRe(x) + i dL/dIm(x) = 2 F^H (w^2 * F x); F^H is the adjoint
+    transform (conjugate direction, no 1/N; Eq. 4)."""
+    X = fft(x, FORWARD)
+    w2 = np.asarray(w, dtype=np.float64) ** 2
+    return 2.0 * fft(w2 * X, ADJOINT)
+
+
+def rel_l2(got, ref) -> float:
+    """||got - ref||_2 / ||ref||_2 over all elements, in FP64."""
+    g = np.asarray(got, dtype=np.complex128)
+    r = np.asarray(ref, dtype=np.complex128)
+    den = np.sqrt(np.sum(np.abs(r) ** 2))
+    num = np.sqrt(np.sum(np.abs(g - r) ** 2))
+    return float(num / den) if den > 0 else float(num)
+
+
+def rel_l2_rows(got, ref) -> np.ndarray:
+    """Relative L2 error of each transform (last axis) separately."""
+    g = np.asarray(got, dtype=np.complex128)
+    r = np.asarray(ref, dtype=np.complex128)
+    den = np.sqrt(np.sum(np.abs(r) ** 2, axis=-1))
+    num = np.sqrt(np.sum(np.abs(g - r) ** 2, axis=-1))
+    return num / np.where(den > 0, den, 1.0)

@@ -1,0 +1,187 @@
+"""Pins for the FP64 oracle: checks that tie it to something other than itself.
+
+Each check takes the oracle's compiled library (so the mutation test can run
+the same battery against deliberately broken copies) and raises
+AssertionError on failure.  Sources of truth, none of them the oracle:
+
+* hand-worked values from Eq. 1 / Eq. 2 (tests/golden/dft_worked_examples.txt);
+* the N=2 butterfly and the N=4 DFT matrix written out by hand;
+* closed forms: delta, shifted delta, single tone, constant, cosine;
+* invariants: Parseval, linearity, inverse round trip, Hermitian symmetry of
+  a real input's spectrum, the circular shift theorem, the adjoint identity;
+* brute force (the O(N^2) sum) against the radix-2 recursion;
+* an independent library routine: numpy's pocketfft in FP64.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "dft_worked_examples.txt")
+
+TIGHT = 1e-12     # FP64 oracle tolerance (relative L2) for O(N log N)-size sums
+
+
+def _rng(seed=1):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _cvec(n, seed=1, batch=None):
+    g = _rng(seed)
+    shape = (n,) if batch is None else (batch, n)
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+def _close(got, ref, tol, what):
+    err = oracle.rel_l2(got, ref) if np.linalg.norm(ref) > 0 else float(np.max(np.abs(got - ref)))
+    assert err <= tol, f"{what}: relative error {err:.3e} > {tol:.1e}"
+
+
+def load_golden():
+    cases = []
+    cur = None
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tok = line.split()
+            if tok[0] == "example":
+                cur = {"name": tok[1], "dir": tok[2], "n": int(tok[3])}
+                cases.append(cur)
+            elif tok[0] in ("in", "out"):
+                vals = [complex(float(p.split(",")[0]), float(p.split(",")[1])) for p in tok[1:]]
+                cur[tok[0]] = np.array(vals, dtype=np.complex128)
+    for c in cases:
+        assert len(c["in"]) == c["n"] and len(c["out"]) == c["n"], c["name"]
+    return cases
+
+
+def check_golden(lib):
+    for c in load_golden():
+        d = oracle.FORWARD if c["dir"] == "fwd" else oracle.INVERSE
+        for fn in (oracle.dft, oracle.fft):
+            got = fn(c["in"], d, lib=lib)
+            assert np.max(np.abs(got - c["out"])) <= 1e-12 * max(1.0, np.max(np.abs(c["out"]))), \
+                f"golden {c['name']} via {fn.__name__}: {got} vs {c['out']}"
+
+
+def check_small_by_hand(lib):
+    a, b = 0.3 - 1.1j, -2.0 + 0.5j
+    for fn in (oracle.dft, oracle.fft):
+        got = fn(np.array([a, b]), oracle.FORWARD, lib=lib)
+        assert np.allclose(got, [a + b, a - b], rtol=0, atol=1e-15), f"N=2 butterfly via {fn.__name__}"
+        got = fn(np.array([a, b]), oracle.INVERSE, lib=lib)
+        assert np.allclose(got, [(a + b) / 2, (a - b) / 2], rtol=0, atol=1e-15), f"N=2 inverse via {fn.__name__}"
+    # The 4-point DFT matrix, entries W_4^{nk} = (-i)^{nk}, written out by hand.
+    F4 = np.array([[1, 1, 1, 1],
+                   [1, -1j, -1, 1j],
+                   [1, -1, 1, -1],
+                   [1, 1j, -1, -1j]], dtype=np.complex128)
+    x = _cvec(4, seed=7)
+    ref = F4 @ x
+    for fn in (oracle.dft, oracle.fft):
+        _close(fn(x, oracle.FORWARD, lib=lib), ref, 1e-15, f"N=4 matrix via {fn.__name__}")
+        _close(fn(x, oracle.ADJOINT, lib=lib), F4.conj().T @ x, 1e-15, f"N=4 adjoint via {fn.__name__}")
+        _close(fn(x, oracle.INVERSE, lib=lib), F4.conj().T @ x / 4, 1e-15, f"N=4 inverse via {fn.__name__}")
+
+
+def check_closed_forms(lib, sizes=(2, 8, 64, 256, 1024, 4096)):
+    for n in sizes:
+        fns = (oracle.dft, oracle.fft) if n <= 1024 else (oracle.fft,)
+        k = np.arange(n)
+        for fn in fns:
+            tag = f"{fn.__name__} N={n}"
+            delta = np.zeros(n, complex)
+            delta[0] = 1
+            _close(fn(delta, lib=lib), np.ones(n), 1e-14, f"delta {tag}")
+            n0 = (3 * n) // 7 + 1 if n > 2 else 1
+            sd = np.zeros(n, complex)
+            sd[n0] = 1
+            ramp = np.exp(-2j * np.pi * ((k * n0) % n) / n)
+            _close(fn(sd, lib=lib), ramp, 1e-13, f"shifted delta {tag}")
+            m = (5 * n) // 11 % n
+            tone = np.exp(2j * np.pi * ((k * m) % n) / n)
+            spike = np.zeros(n, complex)
+            spike[m] = n
+            _close(fn(tone, lib=lib), spike, 1e-13, f"tone {tag}")
+            const = np.full(n, 2.5 - 0.5j)
+            cs = np.zeros(n, complex)
+            cs[0] = n * (2.5 - 0.5j)
+            _close(fn(const, lib=lib), cs, 1e-14, f"constant {tag}")
+            if n >= 4:
+                mc = max(1, n // 4 - 1)
+                cosine = np.cos(2 * np.pi * ((k * mc) % n) / n).astype(complex)
+                two = np.zeros(n, complex)
+                two[mc] = n / 2
+                two[n - mc] = n / 2
+                _close(fn(cosine, lib=lib), two, 1e-13, f"cosine {tag}")
+
+
+def check_invariants(lib, sizes=(16, 512, 2048, 16384)):
+    for n in sizes:
+        fn = oracle.dft if n <= 512 else oracle.fft
+        x = _cvec(n, seed=n)
+        y = _cvec(n, seed=n + 1)
+        X = fn(x, lib=lib)
+        Y = fn(y, lib=lib)
+        # Parseval: sum |X|^2 = N sum |x|^2
+        px, pX = np.sum(np.abs(x) ** 2), np.sum(np.abs(X) ** 2)
+        assert abs(pX - n * px) <= 1e-12 * n * px, f"Parseval N={n}"
+        # linearity
+        a, b = 0.7 - 0.2j, -1.3 + 2.0j
+        _close(fn(a * x + b * y, lib=lib), a * X + b * Y, 1e-13, f"linearity N={n}")
+        # round trip (Eq. 2 undoes Eq. 1)
+        _close(fn(X, oracle.INVERSE, lib=lib), x, TIGHT, f"round trip N={n}")
+        # Hermitian symmetry for a real input: X(N-k) = conj X(k)
+        r = fn(x.real.astype(complex), lib=lib)
+        _close(r[(-np.arange(n)) % n], np.conj(r), 1e-13, f"Hermitian N={n}")
+        # circular shift theorem: x(n - s) -> W_N^{sk} X(k)
+        s = n // 3 + 1
+        ph = np.exp(-2j * np.pi * ((np.arange(n) * s) % n) / n)
+        _close(fn(np.roll(x, s), lib=lib), ph * X, 1e-13, f"shift N={n}")
+        # adjoint identity <F x, y> = <x, F^H y>
+        lhs = np.vdot(y, X)
+        rhs = np.vdot(fn(y, oracle.ADJOINT, lib=lib), x)
+        assert abs(lhs - rhs) <= 1e-12 * n * np.linalg.norm(x) * np.linalg.norm(y), f"adjoint N={n}"
+
+
+def check_dft_vs_fft(lib, max_log2=10):
+    for lg in range(1, max_log2 + 1):
+        n = 1 << lg
+        x = _cvec(n, seed=100 + lg, batch=3)
+        for d in (oracle.FORWARD, oracle.INVERSE, oracle.ADJOINT):
+            _close(oracle.fft(x, d, lib=lib), oracle.dft(x, d, lib=lib), 1e-13, f"dft vs fft N={n} dir={d}")
+
+
+def check_numpy(lib, sizes=(2, 4, 32, 1024, 4096, 65536)):
+    for n in sizes:
+        x = _cvec(n, seed=200 + n, batch=2)
+        fns = (oracle.fft, oracle.dft) if n <= 1024 else (oracle.fft,)
+        for fn in fns:
+            _close(fn(x, oracle.FORWARD, lib=lib), np.fft.fft(x, axis=-1), 1e-13, f"numpy fwd {fn.__name__} N={n}")
+            _close(fn(x, oracle.INVERSE, lib=lib), np.fft.ifft(x, axis=-1), 1e-13, f"numpy inv {fn.__name__} N={n}")
+            _close(fn(x, oracle.ADJOINT, lib=lib), n * np.fft.ifft(x, axis=-1), 1e-13, f"numpy adj {fn.__name__} N={n}")
+
+
+def check_fft2(lib, shapes=((4, 8), (32, 16), (64, 128))):
+    for ny, nx in shapes:
+        g = _rng(ny * 1000 + nx)
+        x = g.standard_normal((ny, nx)) + 1j * g.standard_normal((ny, nx))
+        _close(oracle.fft2(x, oracle.FORWARD, lib=lib), np.fft.fft2(x), 1e-13, f"fft2 {ny}x{nx}")
+        _close(oracle.fft2(x, oracle.INVERSE, lib=lib), np.fft.ifft2(x), 1e-13, f"ifft2 {ny}x{nx}")
+        # 2-D closed form: a delta at (y0, x0) -> W_ny^{y0 ky} W_nx^{x0 kx}
+        d = np.zeros((ny, nx), complex)
+        y0, x0 = ny // 3, nx // 5 + 1
+        d[y0, x0] = 1
+        ky, kx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        ref = np.exp(-2j * np.pi * (((ky * y0) % ny) / ny + ((kx * x0) % nx) / nx))
+        _close(oracle.fft2(d, lib=lib), ref, 1e-13, f"fft2 delta {ny}x{nx}")
+
+
+ALL_CHECKS = (check_golden, check_small_by_hand, check_closed_forms, check_invariants,
+              check_dft_vs_fft, check_numpy, check_fft2)

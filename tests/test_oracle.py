@@ -1,0 +1,114 @@
+"""CPU-only tests that pin the FP64 oracle (no GPU, no CUDA library)."""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins as pins
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return oracle.load_library()
+
+
+@pytest.mark.parametrize("check", pins.ALL_CHECKS, ids=lambda c: c.__name__)
+def test_pin(lib, check):
+    check(lib)
+
+
+def test_rejects_bad_arguments(lib):
+    with pytest.raises(ValueError):
+        oracle.fft(np.ones(12, complex), lib=lib)   # not a power of two
+    with pytest.raises(ValueError):
+        oracle.fft(np.ones(8, complex), dir=5, lib=lib)
+    # the O(N^2) sum accepts any length (Eq. 1 has no power-of-two condition)
+    x = pins._cvec(12, seed=3)
+    assert oracle.rel_l2(oracle.dft(x, lib=lib), np.fft.fft(x)) < 1e-14
+
+
+def test_transform_route(lib):
+    x = pins._cvec(2048, seed=5)
+    assert oracle.rel_l2(oracle.transform(x), np.fft.fft(x)) < 1e-13
+    y = pins._cvec(256, seed=6)
+    assert oracle.rel_l2(oracle.transform(y), np.fft.fft(y)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [16, 64, 256])
+def test_loss_gradient_finite_differences(n):
+    """L = sum |w X|^2 is quadratic in (Re x, Im x), so a central difference is
+    exact up to rounding: compare every component of the oracle gradient."""
+    g = np.random.Generator(np.random.PCG64(n))
+    x = g.standard_normal(n) + 1j * g.standard_normal(n)
+    w = g.uniform(0, 1, n)
+    grad = oracle.spectral_loss_grad(x, w)
+    h = 1e-3
+    fd = np.empty(n, complex)
+    for i in range(n):
+        for part, unit in ((0, 1.0), (1, 1j)):
+            xp = x.copy()
+            xm = x.copy()
+            xp[i] += h * unit
+            xm[i] -= h * unit
+            d = (oracle.spectral_loss(xp, w) - oracle.spectral_loss(xm, w)) / (2 * h)
+            if part == 0:
+                fd[i] = d
+            else:
+                fd[i] += 1j * d
+    assert oracle.rel_l2(grad, fd) < 1e-9
+
+
+def test_loss_gradient_closed_form():
+    """With w = 1, L = ||F x||^2 = N ||x||^2 (Parseval), so the gradient is 2 N x."""
+    n = 128
+    g = np.random.Generator(np.random.PCG64(9))
+    x = g.standard_normal(n) + 1j * g.standard_normal(n)
+    assert oracle.rel_l2(oracle.spectral_loss_grad(x, np.ones(n)), 2 * n * x) < 1e-13
+    assert abs(oracle.spectral_loss(x, np.ones(n)) - n * np.sum(np.abs(x) ** 2)) < 1e-10 * n * n
+
+
+# --- the pins must catch plausible mistakes ---------------------------------
+# Each mutation is planted in a temporary copy of the oracle's C source, on the
+# CPU; the battery above must then fail at least once.
+MUTATIONS = {
+    "wrong_sign": ("*wi = (double)s * sin(a);", "*wi = -(double)s * sin(a);"),
+    "dropped_term": ("acc_i += xr * wi + xi * wr;", "acc_i += xr * wi;"),
+    "butterfly_sign": ("y[2 * (h + k)] = er - tr;", "y[2 * (h + k)] = er + tr;"),
+    "butterfly_index": ("oracle_w(k, n, s, &wr, &wi);", "oracle_w(k, h, s, &wr, &wi);"),
+    "no_inverse_scale": ("return dir == 1 ? 1.0 / (double)n : 1.0;", "return 1.0;"),
+    "transposed_2d": ("col[2 * y] = out[2 * (y * nx + x)];", "col[2 * y] = out[2 * (x * nx + y)];"),
+    "swapped_halves": ("fft_rec(h, x, 2 * stride, y, s);", "fft_rec(h, x + 2 * stride, 2 * stride, y, s);"),
+}
+
+
+def _mutated_lib(tmpdir, name, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "fft_oracle.c")).read()
+    assert old in src, f"mutation {name}: anchor not found"
+    path = os.path.join(tmpdir, f"{name}.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new, 1))
+    so = os.path.join(tmpdir, f"lib{name}.so")
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", path, "-o", so, "-lm"])
+    return oracle.load_library(so)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    old, new = MUTATIONS[name]
+    with tempfile.TemporaryDirectory() as d:
+        lib = _mutated_lib(d, name, old, new)
+        failures = 0
+        for check in pins.ALL_CHECKS:
+            try:
+                check(lib)
+            except (AssertionError, ValueError):
+                failures += 1
+        assert failures > 0, f"no pin caught mutation {name}"
