@@ -1,0 +1,139 @@
+/*
+ * gbfft.h -- C ABI of the GB300 (sm_103a) power-of-two complex FFT library.
+ *
+ * What the library computes (paper Sec. 2.1):
+ *   forward  (Eq. 1):  X(k) = sum_{n=0}^{N-1} x(n) W_N^{nk},            W_N = exp(-2*pi*i/N)
+ *   inverse  (Eq. 2):  x(n) = (1/N) sum_{k=0}^{N-1} X(k) W_N^{-nk}
+ *   adjoint  (Eq. 4):  the conjugate-direction sum without the 1/N, i.e. F^H.
+ * Outputs are in natural order.  Data are complex64: interleaved (re, im)
+ * float32 pairs, contiguous; a batch of B transforms of length N is B*N
+ * complex values with transform b at offset b*N.  2-D images are row-major
+ * (element (y, x) at y*nx + x).
+ *
+ * Memory: every data pointer passed to fft_exec* is a DEVICE pointer owned by
+ * the caller, at least 8-byte aligned (FFT_ERR_ALIGN otherwise).  in == out
+ * (in place) is allowed for every plan kind.  The library allocates only at
+ * plan creation (the twiddle tables) and in fft_plan_set_workspace(plan, NULL);
+ * fft_exec* never allocates, never synchronises the stream and is safe to
+ * capture into a CUDA graph.
+ *
+ * Errors: calls return 0 (FFT_OK) or a negative FFT_ERR_* code; plan
+ * constructors return NULL on error.  The code of the last failing call on
+ * the calling host thread is kept in fft_last_error().  Argument errors are
+ * detected on the host before anything is launched.
+ */
+#ifndef GBFFT_H
+#define GBFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GBFFT_API __attribute__((visibility("default")))
+#else
+#define GBFFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft_plan fft_plan; /* opaque, owned by the library */
+
+/* Directions.  FFT_ADJOINT is a flag: FFT_ADJOINT alone is the adjoint of the
+ * forward transform (conjugate direction, no scale, Eq. 4), and
+ * FFT_INVERSE | FFT_ADJOINT is the adjoint of the inverse (forward direction
+ * with 1/N). */
+enum { FFT_FORWARD = 0, FFT_INVERSE = 1, FFT_ADJOINT = 2 };
+
+/* Arithmetic of the radix-16 passes.  FP32 is the plain path.  The TC_*
+ * variants run each radix-16 DFT as a small dense product on the tensor cores
+ * (BF16 or FP16 operands, FP32 accumulation); *_SPLIT adds hi+lo operand
+ * splitting (three products) to win back accuracy.  Twiddles stay FP32. */
+enum {
+  FFT_PREC_FP32 = 0,
+  FFT_PREC_TC_BF16 = 1,
+  FFT_PREC_TC_FP16 = 2,
+  FFT_PREC_TC_BF16_SPLIT = 3,
+  FFT_PREC_TC_FP16_SPLIT = 4
+};
+
+enum {
+  FFT_OK = 0,
+  FFT_ERR_INVALID_ARG = -1,   /* n not a power of two, n < 2, n too large, batch < 1, bad dir/prec, NULL */
+  FFT_ERR_ALIGN = -2,         /* data pointer not 8-byte aligned */
+  FFT_ERR_NO_WORKSPACE = -3,  /* plan needs a workspace and none was set */
+  FFT_ERR_CUDA = -4,          /* a CUDA runtime call or launch failed */
+  FFT_ERR_TIMEOUT = -5,       /* a bounded device-side wait ran out */
+  FFT_ERR_UNSUPPORTED = -6,   /* valid request this build does not implement */
+  FFT_ERR_ALLOC = -7          /* host or device allocation failed at plan time */
+};
+
+/* Largest supported 1-D length (2^28) and 2-D side (2^14). */
+#define FFT_MAX_LOG2N 28
+#define FFT_MAX_LOG2_SIDE 14
+
+/* Plan for `batch` 1-D transforms of length n (power of two, 2 <= n <= 2^28).
+ * dir is the direction fft_exec uses (FFT_FORWARD, FFT_INVERSE, optionally
+ * with FFT_ADJOINT); prec one of FFT_PREC_*.  Lengths up to 2^14 run as one
+ * on-chip pass per transform (Sec. 2.3.2, "no need to divide"); longer ones
+ * are split N = N1*N2 into a column pass with twiddle scaling and a row pass
+ * through global memory (Sec. 2.3.2, "two times exchange").
+ * Builds the twiddle tables on the current device (FP64 sincospi rounded
+ * once to FP32; Sec. 2.3.1 look-up table).  Returns NULL on error. */
+GBFFT_API fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec);
+
+/* Plan for `batch` 2-D transforms of ny-by-nx row-major images (powers of two,
+ * 2 <= ny, nx <= 2^14): 1-D transforms of every row, then of every column
+ * (Sec. 2.3.2: rows, then columns). */
+GBFFT_API fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int prec);
+
+/* Plan for `count` 1-D transforms of uneven power-of-two lengths lengths[i]
+ * (2^1..2^16), packed back to back: transform i starts at the prefix sum of
+ * the lengths before it.  The host array is copied; the caller keeps it. */
+GBFFT_API fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, int prec);
+
+/* Runs the plan on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Asynchronous.  in/out: device pointers to the packed complex64 data. */
+GBFFT_API int fft_exec(fft_plan* plan, const void* in, void* out, void* stream);
+
+/* As fft_exec, with an explicit direction instead of the plan's (the twiddle
+ * tables serve every direction); used for the adjoint in backpropagation. */
+GBFFT_API int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* stream);
+
+/* Frees the plan and everything the library allocated for it.  NULL-safe.
+ * The caller must not use the plan afterwards. */
+GBFFT_API void fft_destroy(fft_plan* plan);
+
+/* Bytes of device workspace fft_exec needs (0 for single-pass and 2-D plans). */
+GBFFT_API size_t fft_plan_workspace_bytes(const fft_plan* plan);
+
+/* Gives the plan a caller-owned device workspace of at least
+ * fft_plan_workspace_bytes(plan) bytes (256-byte aligned), or, with NULL, makes
+ * the library allocate and own one now.  Returns FFT_OK or an error code. */
+GBFFT_API int fft_plan_set_workspace(fft_plan* plan, void* dev_ptr);
+
+/* Descriptive queries (for tests and the benchmark). */
+GBFFT_API int64_t fft_plan_length(const fft_plan* plan);
+GBFFT_API int64_t fft_plan_batch(const fft_plan* plan);
+/* Number of kernel launches one fft_exec issues. */
+GBFFT_API int fft_plan_launches(const fft_plan* plan);
+/* Kind: 0 single on-chip pass, 1 four-step, 2 two-dimensional, 3 uneven batch. */
+GBFFT_API int fft_plan_kind(const fft_plan* plan);
+/* Human-readable plan summary into buf (NUL-terminated); returns FFT_OK. */
+GBFFT_API int fft_plan_describe(const fft_plan* plan, char* buf, size_t len);
+
+/* Device-side status word of the plan (0 = OK, FFT_ERR_TIMEOUT if a bounded
+ * wait gave up).  Synchronises `stream` to read it. */
+GBFFT_API int fft_status(fft_plan* plan, void* stream);
+
+/* Code of the last failing call on this host thread (FFT_OK if none). */
+GBFFT_API int fft_last_error(void);
+/* Static description of an error code. */
+GBFFT_API const char* fft_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFFT_H */

@@ -1,0 +1,82 @@
+"""ctypes loader for ``libgbfft.so`` (the C ABI declared in include/gbfft.h).
+
+Argument marshalling only: every step of a transform runs in the library's
+CUDA kernels.  Importing this module never builds anything; a missing library
+raises immediately so no caller can fall back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbfft.so")
+
+FFT_FORWARD, FFT_INVERSE, FFT_ADJOINT = 0, 1, 2
+FFT_PREC_FP32, FFT_PREC_TC_BF16, FFT_PREC_TC_FP16, FFT_PREC_TC_BF16_SPLIT, FFT_PREC_TC_FP16_SPLIT = range(5)
+
+FFT_OK = 0
+ERRORS = {
+    -1: "FFT_ERR_INVALID_ARG",
+    -2: "FFT_ERR_ALIGN",
+    -3: "FFT_ERR_NO_WORKSPACE",
+    -4: "FFT_ERR_CUDA",
+    -5: "FFT_ERR_TIMEOUT",
+    -6: "FFT_ERR_UNSUPPORTED",
+    -7: "FFT_ERR_ALLOC",
+}
+
+# name -> (restype, argtypes); the full exported surface of include/gbfft.h
+_i64, _int, _vp, _sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+SIGNATURES = {
+    "fft_plan_create": (_vp, [_i64, _i64, _int, _int]),
+    "fft_plan_create_2d": (_vp, [_i64, _i64, _i64, _int, _int]),
+    "fft_plan_create_many": (_vp, [ctypes.POINTER(_i64), _i64, _int, _int]),
+    "fft_exec": (_int, [_vp, _vp, _vp, _vp]),
+    "fft_exec_dir": (_int, [_vp, _vp, _vp, _int, _vp]),
+    "fft_destroy": (None, [_vp]),
+    "fft_plan_workspace_bytes": (_sz, [_vp]),
+    "fft_plan_set_workspace": (_int, [_vp, _vp]),
+    "fft_plan_length": (_i64, [_vp]),
+    "fft_plan_batch": (_i64, [_vp]),
+    "fft_plan_launches": (_int, [_vp]),
+    "fft_plan_kind": (_int, [_vp]),
+    "fft_plan_describe": (_int, [_vp, ctypes.c_char_p, _sz]),
+    "fft_status": (_int, [_vp, _vp]),
+    "fft_last_error": (_int, []),
+    "fft_error_string": (ctypes.c_char_p, [_int]),
+}
+
+_lib = None
+
+
+class GbfftError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        name = ERRORS.get(code, str(code))
+        super().__init__(f"{what}: {name}" if what else name)
+
+
+def load(path: str | None = None):
+    """Load the library once; raise if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with __graft_entry__.build() "
+                           "(there is no fallback implementation)")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def check(code: int, what: str = "") -> int:
+    if code != FFT_OK:
+        raise GbfftError(code, what)
+    return code

@@ -1,0 +1,221 @@
+"""PyTorch-facing API: plans over the C ABI plus autograd Functions.
+
+PyTorch supplies device memory and streams only.  Every transform, inverse
+and adjoint runs in libgbfft's CUDA kernels; if the library or a GPU is
+missing these calls raise instead of computing anything another way.
+
+Conventions (paper Sec. 2.1): ``fft`` is Eq. 1 with W_N = exp(-2*pi*i/N),
+``ifft`` is Eq. 2 (with 1/N), natural-order outputs.  Gradients follow
+PyTorch's complex convention: for y = F x the backward pass returns F^H g,
+which is the adjoint transform (conjugate direction, no 1/N, Eq. 4); for
+y = F^{-1} x it returns (1/N) F g.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _lib as L
+
+FORWARD, INVERSE, ADJOINT = L.FFT_FORWARD, L.FFT_INVERSE, L.FFT_ADJOINT
+PREC = {
+    "fp32": L.FFT_PREC_FP32,
+    "tc_bf16": L.FFT_PREC_TC_BF16,
+    "tc_fp16": L.FFT_PREC_TC_FP16,
+    "tc_bf16_split": L.FFT_PREC_TC_BF16_SPLIT,
+    "tc_fp16_split": L.FFT_PREC_TC_FP16_SPLIT,
+}
+
+
+def _prec_code(prec) -> int:
+    if isinstance(prec, int):
+        return prec
+    return PREC[prec]
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Plan:
+    """Owns one library plan and (for four-step plans) its torch-allocated
+    workspace.  ``kind`` is "1d", "2d" or "many"."""
+
+    def __init__(self, kind: str, shape, batch: int = 1, dir: int = FORWARD, prec="fp32",
+                 device=None, lengths=None):
+        self.lib = L.load()
+        self.kind = kind
+        self.shape = tuple(shape)
+        self.batch = int(batch)
+        self.dir = int(dir)
+        self.prec = _prec_code(prec)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            if kind == "1d":
+                h = self.lib.fft_plan_create(int(shape[0]), self.batch, self.dir, self.prec)
+            elif kind == "2d":
+                h = self.lib.fft_plan_create_2d(int(shape[0]), int(shape[1]), self.batch, self.dir, self.prec)
+            elif kind == "many":
+                arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
+                self.lengths = [int(v) for v in lengths]
+                h = self.lib.fft_plan_create_many(arr, len(lengths), self.dir, self.prec)
+            else:
+                raise ValueError(kind)
+            if not h:
+                raise L.GbfftError(self.lib.fft_last_error(), f"plan {kind} {shape} batch={batch} prec={prec}")
+            self.handle = ctypes.c_void_p(h)
+            self.ws_bytes = int(self.lib.fft_plan_workspace_bytes(self.handle))
+            self.workspace = None
+            if self.ws_bytes:
+                # the workspace belongs to torch; the library only borrows it
+                self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+                ptr = self.workspace.data_ptr()
+                ptr = (ptr + 255) & ~255
+                L.check(self.lib.fft_plan_set_workspace(self.handle, ctypes.c_void_p(ptr)), "set_workspace")
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.fft_plan_launches(self.handle))
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        self.lib.fft_plan_describe(self.handle, buf, 512)
+        return buf.value.decode()
+
+    def exec_ptr(self, in_ptr: int, out_ptr: int, dir: int | None = None, stream=None) -> None:
+        d = self.dir if dir is None else int(dir)
+        rc = self.lib.fft_exec_dir(self.handle, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), d,
+                                   ctypes.c_void_p(_stream_handle(stream)))
+        L.check(rc, "fft_exec")
+
+    def __call__(self, x: torch.Tensor, out: torch.Tensor | None = None, dir: int | None = None,
+                 stream=None) -> torch.Tensor:
+        if x.dtype != torch.complex64 or not x.is_cuda:
+            raise TypeError("expected a complex64 CUDA tensor")
+        x = x.contiguous()
+        if out is None:
+            out = torch.empty_like(x)
+        self.exec_ptr(x.data_ptr(), out.data_ptr(), dir, stream)
+        return out
+
+    def status(self, stream=None) -> int:
+        return int(self.lib.fft_status(self.handle, ctypes.c_void_p(_stream_handle(stream))))
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.lib.fft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_cache: dict = {}
+_cache_lock = threading.Lock()
+
+
+def get_plan(kind: str, shape, batch: int, prec="fp32", device=None, lengths=None) -> Plan:
+    """Cached plan (twiddle tables are built once per shape/precision/device)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    key = (kind, tuple(shape), int(batch), _prec_code(prec), dev.index, tuple(lengths) if lengths is not None else None)
+    with _cache_lock:
+        p = _cache.get(key)
+        if p is None:
+            p = Plan(kind, shape, batch, FORWARD, prec, dev, lengths)
+            _cache[key] = p
+        return p
+
+
+def clear_plan_cache() -> None:
+    with _cache_lock:
+        for p in _cache.values():
+            p.close()
+        _cache.clear()
+
+
+def _check_input(x: torch.Tensor, min_dims: int = 1) -> None:
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.complex64 or not x.is_cuda:
+        raise TypeError("expected a complex64 CUDA tensor")
+    if x.dim() < min_dims:
+        raise ValueError(f"expected at least {min_dims} dimension(s)")
+
+
+class _FFT1d(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, dir, prec):
+        n = x.shape[-1]
+        batch = x.numel() // n if n else 0
+        plan = get_plan("1d", (n,), batch, prec, x.device)
+        ctx.plan, ctx.dir = plan, dir
+        y = plan(x, dir=dir)
+        return y
+
+    @staticmethod
+    def backward(ctx, g):
+        g = g.contiguous()
+        return ctx.plan(g, dir=ctx.dir ^ ADJOINT), None, None
+
+
+class _FFT2d(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, dir, prec):
+        ny, nx = x.shape[-2], x.shape[-1]
+        batch = x.numel() // (ny * nx)
+        plan = get_plan("2d", (ny, nx), batch, prec, x.device)
+        ctx.plan, ctx.dir = plan, dir
+        return plan(x, dir=dir)
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan(g.contiguous(), dir=ctx.dir ^ ADJOINT), None, None
+
+
+class _FFTMany(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, lengths, dir, prec):
+        plan = get_plan("many", (int(sum(lengths)),), len(lengths), prec, x.device, lengths=tuple(lengths))
+        ctx.plan, ctx.dir = plan, dir
+        return plan(x, dir=dir)
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan(g.contiguous(), dir=ctx.dir ^ ADJOINT), None, None, None
+
+
+def fft(x: torch.Tensor, prec="fp32") -> torch.Tensor:
+    """Eq. 1 over the last dimension (length a power of two, 2..2^28)."""
+    _check_input(x)
+    return _FFT1d.apply(x, FORWARD, prec)
+
+
+def ifft(x: torch.Tensor, prec="fp32") -> torch.Tensor:
+    """Eq. 2 over the last dimension."""
+    _check_input(x)
+    return _FFT1d.apply(x, INVERSE, prec)
+
+
+def fft2(x: torch.Tensor, prec="fp32") -> torch.Tensor:
+    """2-D transform over the last two dimensions (rows, then columns)."""
+    _check_input(x, 2)
+    return _FFT2d.apply(x, FORWARD, prec)
+
+
+def ifft2(x: torch.Tensor, prec="fp32") -> torch.Tensor:
+    _check_input(x, 2)
+    return _FFT2d.apply(x, INVERSE, prec)
+
+
+def fft_many(packed: torch.Tensor, lengths, inverse: bool = False, prec="fp32") -> torch.Tensor:
+    """Transforms of uneven power-of-two lengths packed back to back in a 1-D
+    complex64 tensor (transform i starts at sum(lengths[:i]))."""
+    _check_input(packed)
+    lengths = [int(v) for v in lengths]
+    if packed.numel() != sum(lengths):
+        raise ValueError("packed size does not match the sum of the lengths")
+    return _FFTMany.apply(packed.reshape(-1), lengths, INVERSE if inverse else FORWARD, prec)

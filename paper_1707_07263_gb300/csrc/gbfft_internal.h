@@ -1,0 +1,56 @@
+// gbfft_internal.h -- plan representation shared by the host-side planner and
+// the kernel launchers.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gbfft.h"
+
+namespace gbfft {
+
+struct TileKernelInfo;
+struct ManyPlan;
+
+enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3 };
+
+cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s);
+cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);
+
+}  // namespace gbfft
+
+struct fft_plan {
+  int kind;
+  int64_t n;       // transform length (1-D), ny*nx (2-D), total points (many)
+  int64_t batch;   // transforms (1-D), images (2-D), count (many)
+  int64_t ny, nx;  // 2-D sides
+  int dir, prec;
+  int device;
+
+  // single pass: lg; four-step: lg1 = log2 N1 (column length), lg2 = log2 N2
+  // (row length); 2-D: lg1 = log2 ny, lg2 = log2 nx.
+  int lg, lg1, lg2;
+  int c1, c2;  // transforms per CTA of the first / second pass
+  const gbfft::TileKernelInfo* k1;
+  const gbfft::TileKernelInfo* k2;
+
+  // all twiddle tables live in one device allocation
+  void* d_tables;
+  const float2* tw1;  // stage table for the first pass length
+  const float2* tw2;  // stage table for the second pass length
+  const float2* ft_lo;
+  const float2* ft_hi;
+  int ft_s;
+
+  // tensor-core radix-16 path (prec != FFT_PREC_FP32)
+  void* d_tc;   // DFT matrices (hi/lo splits) in BF16/FP16
+
+  size_t ws_bytes;
+  void* ws;
+  int ws_owned;
+
+  int* d_status;  // device status word (bounded waits)
+
+  gbfft::ManyPlan* many;
+  int launches;
+};

@@ -1,0 +1,522 @@
+// plan.cu -- host-side planner and the C ABI (include/gbfft.h).
+//
+// The planner maps a request onto the tile kernels:
+//   * n <= 2^14: one on-chip pass per transform (paper Sec. 2.3.2: small data
+//     need no division; here the bound is GB300's shared memory and register
+//     file rather than the C2070's).
+//   * n  > 2^14: four-step split N = N1*N2 (Sec. 2.3.2 "two times exchange"):
+//       pass 1  column FFTs of length N1 over stride N2, each output scaled by
+//               W_N^{n2*k1}, written to the workspace as Y[k1][n2];
+//       pass 2  row FFTs of length N2 of Y[k1][.], written transposed to
+//               X[k1 + N1*k2].
+//   * 2-D ny x nx: row FFTs, then column FFTs in place (Sec. 2.3.2: rows,
+//     then columns).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "gbfft_internal.h"
+#include "tile_registry.h"
+
+using namespace gbfft;
+
+namespace gbfft {
+
+// defined in many.cu / tc.cu
+int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count);
+void many_plan_free(fft_plan* p);
+int many_exec(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s);
+int tc_plan_init(fft_plan* p);
+int tc_exec(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s);
+
+thread_local int g_last_error = FFT_OK;
+
+int set_err(int code) {
+  if (code != FFT_OK) g_last_error = code;
+  return code;
+}
+
+const TileKernelInfo* tile_kernel(int map, int lg, int C) {
+  switch (map) {
+    case MAP_JJ:
+      return (C == jj_cols(lg)) ? tile_kernel_jj(lg) : nullptr;
+    case MAP_CC:
+      if (lg <= 7) return tile_kernel_cc_a(lg, C);
+      if (lg <= 10) return tile_kernel_cc_b(lg, C);
+      return tile_kernel_cc_c(lg, C);
+    case MAP_JC:
+      if (lg <= 8) return tile_kernel_jc_a(lg, C);
+      return tile_kernel_jc_b(lg, C);
+  }
+  return nullptr;
+}
+
+static int ilog2_exact(int64_t v) {
+  if (v < 1 || (v & (v - 1)) != 0) return -1;
+  int l = 0;
+  while ((1LL << l) < v) ++l;
+  return l;
+}
+
+static int env_int(const char* name, int dflt) {
+  const char* s = getenv(name);
+  return (s && *s) ? atoi(s) : dflt;
+}
+
+static int prepare_kernel(const TileKernelInfo* k) {
+  if (!k) return FFT_ERR_UNSUPPORTED;
+  if (k->smem_bytes > 48 * 1024) {
+    if (cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->smem_bytes) != cudaSuccess)
+      return FFT_ERR_CUDA;
+  }
+  return FFT_OK;
+}
+
+// Columns per CTA for a column (c-fast) pass of length 2^lg: as many adjacent
+// columns as fit a 2^13-point tile (64 KB), at most 16.
+static int default_cols(int lg) {
+  int c = (1 << 13) >> lg;
+  if (c < 1) c = 1;
+  if (c > 16) c = 16;
+  return c;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Allocates and fills the plan's twiddle tables: stage tables for up to two
+// lengths and, for four-step plans, the two-level W_N table.
+static int build_tables(fft_plan* p, int lgA, int lgB, int lgN) {
+  const size_t szA = lgA > 0 ? (size_t)stage_tw_size(lgA) : 0;
+  const size_t szB = lgB > 0 ? (size_t)stage_tw_size(lgB) : 0;
+  size_t lo = 0, hi = 0;
+  if (lgN > 0) {
+    p->ft_s = (lgN + 1) / 2;
+    lo = (size_t)1 << p->ft_s;
+    hi = (size_t)1 << (lgN - p->ft_s);
+  }
+  const size_t offA = 0;
+  const size_t offB = offA + align256(szA * 8 + 8);
+  const size_t offLo = offB + align256(szB * 8 + 8);
+  const size_t offHi = offLo + align256(lo * 8 + 8);
+  const size_t offSt = offHi + align256(hi * 8 + 8);
+  const size_t total = offSt + 256;
+  char* base = nullptr;
+  if (cudaMalloc(&base, total) != cudaSuccess) return FFT_ERR_ALLOC;
+  p->d_tables = base;
+  p->tw1 = (const float2*)(base + offA);
+  p->tw2 = (const float2*)(base + offB);
+  p->ft_lo = (const float2*)(base + offLo);
+  p->ft_hi = (const float2*)(base + offHi);
+  p->d_status = (int*)(base + offSt);
+  cudaStream_t s = 0;
+  if (cudaMemsetAsync(p->d_status, 0, sizeof(int), s) != cudaSuccess) return FFT_ERR_CUDA;
+  if (lgA > 0 && launch_gen_stage_twiddles((float2*)p->tw1, lgA, s) != cudaSuccess) return FFT_ERR_CUDA;
+  if (lgB > 0 && launch_gen_stage_twiddles((float2*)p->tw2, lgB, s) != cudaSuccess) return FFT_ERR_CUDA;
+  if (lgN > 0) {
+    if (launch_gen_power_twiddles((float2*)p->ft_lo, lgN, (long long)lo, 1, s) != cudaSuccess) return FFT_ERR_CUDA;
+    if (launch_gen_power_twiddles((float2*)p->ft_hi, lgN, (long long)hi, (long long)lo, s) != cudaSuccess)
+      return FFT_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FFT_ERR_CUDA;
+  return FFT_OK;
+}
+
+static fft_plan* new_plan() {
+  fft_plan* p = new (std::nothrow) fft_plan;
+  if (!p) return nullptr;
+  memset(p, 0, sizeof(*p));
+  cudaGetDevice(&p->device);
+  return p;
+}
+
+static void free_plan(fft_plan* p) {
+  if (!p) return;
+  if (p->many) many_plan_free(p);
+  if (p->ws_owned && p->ws) cudaFree(p->ws);
+  if (p->d_tc) cudaFree(p->d_tc);
+  if (p->d_tables) cudaFree(p->d_tables);
+  delete p;
+}
+
+static bool valid_dir(int dir) { return dir >= 0 && dir <= 3; }
+static bool valid_prec(int prec) { return prec >= FFT_PREC_FP32 && prec <= FFT_PREC_TC_FP16_SPLIT; }
+
+// Direction -> load/store transform: conjugate direction via conj in/out,
+// 1/N of Eq. 2 folded into the store.
+struct DirXf {
+  int conj;
+  float scale;
+};
+static DirXf dir_xf(int dir, int64_t n) {
+  const int inv = dir & FFT_INVERSE;
+  const int adj = (dir & FFT_ADJOINT) ? 1 : 0;
+  DirXf x;
+  x.conj = inv ^ adj;
+  x.scale = inv ? (float)(1.0 / (double)n) : 1.0f;
+  return x;
+}
+
+static void base_args(TileArgs& a) {
+  memset(&a, 0, sizeof(a));
+  a.stream_in = 1;
+  a.stream_out = 1;
+}
+
+static int launch_tile(const TileKernelInfo* k, const TileArgs& a, long long ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return FFT_OK;
+  if (ntiles > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
+  void* args[] = {(void*)&a};
+  cudaError_t e = cudaLaunchKernel(k->fn, dim3((unsigned)ntiles), dim3(k->threads), args, (size_t)k->smem_bytes, s);
+  return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
+}
+
+static void set_out_xf(TileArgs& a, const DirXf& x) {
+  a.scale_out = (x.conj || x.scale != 1.0f) ? 1 : 0;
+  a.sx = x.scale;
+  a.sy = x.conj ? -x.scale : x.scale;
+}
+
+// ---- single on-chip pass -------------------------------------------------
+static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
+  const DirXf x = dir_xf(dir, p->n);
+  TileArgs a;
+  base_args(a);
+  const int C = p->k1->C;
+  const long long L = p->n;
+  a.in = in;
+  a.out = out;
+  a.tw = p->tw1;
+  a.tiles_per_batch = (p->batch + C - 1) / C;
+  a.in_gstride = a.out_gstride = (long long)C * L;
+  a.in_sc = a.out_sc = L;
+  a.in_sn = a.out_sn = 1;
+  a.ncols = p->batch;
+  a.conj_in = x.conj;
+  set_out_xf(a, x);
+  return launch_tile(p->k1, a, a.tiles_per_batch, s);
+}
+
+// ---- four-step: column pass + twiddle, then row pass ------------------------
+static int exec_fourstep(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
+  if (!p->ws) return FFT_ERR_NO_WORKSPACE;
+  const DirXf x = dir_xf(dir, p->n);
+  const long long N = p->n, N1 = 1LL << p->lg1, N2 = 1LL << p->lg2;
+  float2* ws = (float2*)p->ws;
+  // pass 1: tile g = columns [g*C1, g*C1+C1) of the N1 x N2 view x[N2*n1 + n2]
+  TileArgs a;
+  base_args(a);
+  a.in = in;
+  a.out = ws;
+  a.tw = p->tw1;
+  a.tiles_per_batch = N2 / p->c1;
+  a.in_bstride = a.out_bstride = N;
+  a.in_gstride = a.out_gstride = p->c1;
+  a.in_sc = a.out_sc = 1;
+  a.in_sn = a.out_sn = N2;
+  a.ncols = N2;
+  a.ft_lo = p->ft_lo;
+  a.ft_hi = p->ft_hi;
+  a.ft_lgN = p->lg1 + p->lg2;
+  a.ft_s = p->ft_s;
+  a.conj_in = x.conj;
+  a.stream_out = 0;  // the workspace is read back by pass 2: keep it in L2
+  int rc = launch_tile(p->k1, a, a.tiles_per_batch * p->batch, s);
+  if (rc) return rc;
+  // pass 2: tile g = rows k1 in [g*C2, g*C2+C2) of Y, written to X[k1 + N1*k2]
+  TileArgs b;
+  base_args(b);
+  b.in = ws;
+  b.out = out;
+  b.tw = p->tw2;
+  b.tiles_per_batch = N1 / p->c2;
+  b.in_bstride = b.out_bstride = N;
+  b.in_gstride = (long long)p->c2 * N2;
+  b.in_sc = N2;
+  b.in_sn = 1;
+  b.out_gstride = p->c2;
+  b.out_sc = 1;
+  b.out_sn = N1;
+  b.ncols = N1;
+  b.stream_in = 0;
+  set_out_xf(b, x);
+  return launch_tile(p->k2, b, b.tiles_per_batch * p->batch, s);
+}
+
+// ---- 2-D: rows, then columns in place --------------------------------------
+static int exec_2d(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
+  const DirXf x = dir_xf(dir, p->ny * p->nx);
+  const long long ny = p->ny, nx = p->nx;
+  TileArgs a;
+  base_args(a);
+  const int C = p->k1->C;
+  a.in = in;
+  a.out = out;
+  a.tw = p->tw2;
+  a.tiles_per_batch = (ny * p->batch + C - 1) / C;
+  a.in_gstride = a.out_gstride = (long long)C * nx;
+  a.in_sc = a.out_sc = nx;
+  a.in_sn = a.out_sn = 1;
+  a.ncols = ny * p->batch;
+  a.conj_in = x.conj;
+  a.stream_out = 0;  // read back by the column pass
+  int rc = launch_tile(p->k1, a, a.tiles_per_batch, s);
+  if (rc) return rc;
+  TileArgs b;
+  base_args(b);
+  b.in = out;
+  b.out = out;
+  b.tw = p->tw1;
+  b.tiles_per_batch = nx / p->c2;
+  b.in_bstride = b.out_bstride = ny * nx;
+  b.in_gstride = b.out_gstride = p->c2;
+  b.in_sc = b.out_sc = 1;
+  b.in_sn = b.out_sn = nx;
+  b.ncols = nx;
+  b.stream_in = 0;
+  set_out_xf(b, x);
+  return launch_tile(p->k2, b, b.tiles_per_batch * p->batch, s);
+}
+
+int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
+  if (!p || !in || !out || !valid_dir(dir)) return FFT_ERR_INVALID_ARG;
+  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return FFT_ERR_ALIGN;
+  const float2* fin = (const float2*)in;
+  float2* fout = (float2*)out;
+  int rc;
+  if (p->prec != FFT_PREC_FP32 && p->kind != KIND_MANY) {
+    rc = tc_exec(p, fin, fout, dir, s);
+  } else {
+    switch (p->kind) {
+      case KIND_SINGLE: rc = exec_single(p, fin, fout, dir, s); break;
+      case KIND_FOURSTEP: rc = exec_fourstep(p, fin, fout, dir, s); break;
+      case KIND_2D: rc = exec_2d(p, fin, fout, dir, s); break;
+      case KIND_MANY: rc = many_exec(p, fin, fout, dir, s); break;
+      default: rc = FFT_ERR_INVALID_ARG;
+    }
+  }
+  if (rc == FFT_OK && cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    rc = FFT_ERR_CUDA;
+  }
+  return rc;
+}
+
+// Planner for 1-D lengths: kind, split and kernel variants.
+static int plan_1d(fft_plan* p, int lgN) {
+  if (lgN <= 14) {
+    p->kind = KIND_SINGLE;
+    p->lg = p->lg1 = lgN;
+    p->k1 = tile_kernel(MAP_JJ, lgN, jj_cols(lgN));
+    p->c1 = p->k1 ? p->k1->C : 0;
+    p->launches = 1;
+    int rc = prepare_kernel(p->k1);
+    if (rc) return rc;
+    return build_tables(p, lgN, 0, 0);
+  }
+  p->kind = KIND_FOURSTEP;
+  int lg2 = (lgN + 1) / 2;
+  const int force_lg1 = env_int("GBFFT_FORCE_SPLIT", 0);
+  if (force_lg1 > 0 && force_lg1 < lgN && lgN - force_lg1 <= 14 && force_lg1 <= 14) lg2 = lgN - force_lg1;
+  const int lg1 = lgN - lg2;
+  if (lg1 > 14 || lg2 > 14) return FFT_ERR_UNSUPPORTED;
+  p->lg1 = lg1;
+  p->lg2 = lg2;
+  p->c1 = env_int("GBFFT_FORCE_C1", default_cols(lg1));
+  p->c2 = env_int("GBFFT_FORCE_C2", default_cols(lg2));
+  if (p->c1 > (1 << lg2)) p->c1 = 1 << lg2;
+  if (p->c2 > (1 << lg1)) p->c2 = 1 << lg1;
+  p->k1 = tile_kernel(MAP_CC, lg1, p->c1);
+  p->k2 = tile_kernel(MAP_JC, lg2, p->c2);
+  if (!p->k1 || !p->k2) return FFT_ERR_UNSUPPORTED;
+  p->launches = 2;
+  p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
+  int rc = prepare_kernel(p->k1);
+  if (!rc) rc = prepare_kernel(p->k2);
+  if (rc) return rc;
+  return build_tables(p, lg1, lg2, lgN);
+}
+
+}  // namespace gbfft
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec) {
+  const int lgN = ilog2_exact(n);
+  if (lgN < 1 || lgN > FFT_MAX_LOG2N || batch < 1 || !valid_dir(dir) || !valid_prec(prec)) {
+    set_err(FFT_ERR_INVALID_ARG);
+    return nullptr;
+  }
+  if ((double)n * (double)batch > 9.0e15) {
+    set_err(FFT_ERR_INVALID_ARG);
+    return nullptr;
+  }
+  fft_plan* p = new_plan();
+  if (!p) {
+    set_err(FFT_ERR_ALLOC);
+    return nullptr;
+  }
+  p->n = n;
+  p->batch = batch;
+  p->dir = dir;
+  p->prec = prec;
+  int rc = plan_1d(p, lgN);
+  if (rc == FFT_OK && prec != FFT_PREC_FP32) rc = tc_plan_init(p);
+  if (rc != FFT_OK) {
+    free_plan(p);
+    set_err(rc);
+    return nullptr;
+  }
+  return p;
+}
+
+fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int prec) {
+  const int ly = ilog2_exact(ny), lx = ilog2_exact(nx);
+  if (ly < 1 || lx < 1 || ly > FFT_MAX_LOG2_SIDE || lx > FFT_MAX_LOG2_SIDE || batch < 1 || !valid_dir(dir) ||
+      !valid_prec(prec)) {
+    set_err(FFT_ERR_INVALID_ARG);
+    return nullptr;
+  }
+  if (prec != FFT_PREC_FP32) {
+    set_err(FFT_ERR_UNSUPPORTED);
+    return nullptr;
+  }
+  fft_plan* p = new_plan();
+  if (!p) {
+    set_err(FFT_ERR_ALLOC);
+    return nullptr;
+  }
+  p->kind = KIND_2D;
+  p->n = ny * nx;
+  p->ny = ny;
+  p->nx = nx;
+  p->batch = batch;
+  p->dir = dir;
+  p->prec = prec;
+  p->lg1 = ly;
+  p->lg2 = lx;
+  p->k1 = tile_kernel(MAP_JJ, lx, jj_cols(lx));
+  p->c1 = p->k1 ? p->k1->C : 0;
+  p->c2 = env_int("GBFFT_FORCE_C2", default_cols(ly));
+  if (p->c2 > nx) p->c2 = (int)nx;
+  p->k2 = tile_kernel(MAP_CC, ly, p->c2);
+  p->launches = 2;
+  int rc = (p->k1 && p->k2) ? FFT_OK : FFT_ERR_UNSUPPORTED;
+  if (!rc) rc = prepare_kernel(p->k1);
+  if (!rc) rc = prepare_kernel(p->k2);
+  if (!rc) rc = build_tables(p, ly, lx, 0);
+  if (rc != FFT_OK) {
+    free_plan(p);
+    set_err(rc);
+    return nullptr;
+  }
+  return p;
+}
+
+fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, int prec) {
+  if (!lengths || count < 1 || !valid_dir(dir) || !valid_prec(prec)) {
+    set_err(FFT_ERR_INVALID_ARG);
+    return nullptr;
+  }
+  if (prec != FFT_PREC_FP32) {
+    set_err(FFT_ERR_UNSUPPORTED);
+    return nullptr;
+  }
+  fft_plan* p = new_plan();
+  if (!p) {
+    set_err(FFT_ERR_ALLOC);
+    return nullptr;
+  }
+  p->kind = KIND_MANY;
+  p->dir = dir;
+  p->prec = prec;
+  p->batch = count;
+  int rc = many_plan_init(p, lengths, count);
+  if (rc != FFT_OK) {
+    free_plan(p);
+    set_err(rc);
+    return nullptr;
+  }
+  return p;
+}
+
+int fft_exec(fft_plan* plan, const void* in, void* out, void* stream) {
+  if (!plan) return set_err(FFT_ERR_INVALID_ARG);
+  return set_err(exec_plan(plan, in, out, plan->dir, (cudaStream_t)stream));
+}
+
+int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* stream) {
+  return set_err(exec_plan(plan, in, out, dir, (cudaStream_t)stream));
+}
+
+void fft_destroy(fft_plan* plan) { free_plan(plan); }
+
+size_t fft_plan_workspace_bytes(const fft_plan* plan) { return plan ? plan->ws_bytes : 0; }
+
+int fft_plan_set_workspace(fft_plan* plan, void* dev_ptr) {
+  if (!plan) return set_err(FFT_ERR_INVALID_ARG);
+  if (dev_ptr && ((uintptr_t)dev_ptr & 255)) return set_err(FFT_ERR_ALIGN);
+  if (plan->ws_owned && plan->ws) cudaFree(plan->ws);
+  plan->ws = nullptr;
+  plan->ws_owned = 0;
+  if (dev_ptr) {
+    plan->ws = dev_ptr;
+    return FFT_OK;
+  }
+  if (plan->ws_bytes == 0) return FFT_OK;
+  if (cudaMalloc(&plan->ws, plan->ws_bytes) != cudaSuccess) {
+    plan->ws = nullptr;
+    return set_err(FFT_ERR_ALLOC);
+  }
+  plan->ws_owned = 1;
+  return FFT_OK;
+}
+
+int64_t fft_plan_length(const fft_plan* plan) { return plan ? plan->n : 0; }
+int64_t fft_plan_batch(const fft_plan* plan) { return plan ? plan->batch : 0; }
+int fft_plan_launches(const fft_plan* plan) { return plan ? plan->launches : 0; }
+int fft_plan_kind(const fft_plan* plan) { return plan ? plan->kind : -1; }
+
+int fft_plan_describe(const fft_plan* p, char* buf, size_t len) {
+  if (!p || !buf || len == 0) return set_err(FFT_ERR_INVALID_ARG);
+  static const char* kinds[] = {"single", "fourstep", "2d", "many"};
+  snprintf(buf, len,
+           "kind=%s n=%lld batch=%lld lg1=%d lg2=%d c1=%d c2=%d threads1=%d smem1=%d threads2=%d smem2=%d "
+           "prec=%d launches=%d ws=%zu",
+           kinds[p->kind & 3], (long long)p->n, (long long)p->batch, p->lg1, p->lg2, p->c1, p->c2,
+           p->k1 ? p->k1->threads : 0, p->k1 ? p->k1->smem_bytes : 0, p->k2 ? p->k2->threads : 0,
+           p->k2 ? p->k2->smem_bytes : 0, p->prec, p->launches, p->ws_bytes);
+  return FFT_OK;
+}
+
+int fft_status(fft_plan* plan, void* stream) {
+  if (!plan || !plan->d_status) return set_err(FFT_ERR_INVALID_ARG);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+    return set_err(FFT_ERR_CUDA);
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return set_err(FFT_ERR_CUDA);
+  return h;
+}
+
+int fft_last_error(void) { return g_last_error; }
+
+const char* fft_error_string(int code) {
+  switch (code) {
+    case FFT_OK: return "ok";
+    case FFT_ERR_INVALID_ARG: return "invalid argument";
+    case FFT_ERR_ALIGN: return "data pointer not aligned";
+    case FFT_ERR_NO_WORKSPACE: return "plan needs a workspace (fft_plan_set_workspace)";
+    case FFT_ERR_CUDA: return "CUDA runtime error";
+    case FFT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case FFT_ERR_UNSUPPORTED: return "unsupported configuration";
+    case FFT_ERR_ALLOC: return "allocation failed";
+  }
+  return "unknown error";
+}
+
+}  // extern "C"

@@ -1,0 +1,290 @@
+// tile_fft.cuh -- the on-chip sub-FFT: one CTA transforms a tile of C
+// power-of-two transforms of length L = 2^LG entirely in registers and shared
+// memory (paper Sec. 2.3.2: every butterfly level runs in shared memory; global
+// memory is touched once to load the piece and once to store it).
+//
+// Algorithm: Stockham autosort radix-R passes (natural-order output, no bit
+// reversal).  With Ns = product of the radices already applied, pass s takes,
+// for each butterfly j in [0, L/R):
+//     v[r] = a[j + r*L/R] * W_{Ns*R}^{r*(j mod Ns)},   r = 0..R-1
+//     V    = R-point DFT of v
+//     b[(j div Ns)*Ns*R + (j mod Ns) + q*Ns] = V[q],   q = 0..R-1
+// After the last pass Ns*R = L and b holds X(k) of Eq. 1 in natural order.
+// Radices: one remainder pass of radix 2/4/8 first (if LG is not a multiple
+// of 4), then radix-16 passes.  Each thread owns P = min(16, L) points.
+//
+// Data movement: the first pass reads straight from global memory into
+// registers, the last pass writes straight from registers to global memory;
+// the passes in between exchange through a padded shared-memory tile
+// (index n -> n + n/16, plus a per-configuration row pad) that keeps every
+// warp-wide 8-byte access at the 2-wavefront minimum (the paper's Sec. 2.3.3
+// pads its 16x33 array for the same reason; GB300 has 32 banks of 4 bytes).
+//
+// Two thread mappings per pass:
+//   j-fast: consecutive lanes take consecutive butterflies j of one
+//           transform -- coalesced when a transform's points are contiguous.
+//   c-fast: consecutive lanes take the same j of adjacent transforms c --
+//           coalesced when the C transforms are adjacent columns (the
+//           paper's "first dimension is 16" column pass, Sec. 2.3.2).
+// IN_CF / OUT_CF select c-fast for the global-facing first / last pass.
+//
+// Direction (Eq. 2, Eq. 4): the kernels always apply the forward W_N; the
+// conjugate direction is obtained as conj(F(conj(x))), i.e. by negating the
+// imaginary part on load and on store, and the 1/N of Eq. 2 is folded into
+// the store.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_common.cuh"
+
+namespace gbfft {
+
+// ---------------------------------------------------------------------------
+// Radix schedule for L = 2^LG: remainder pass first, then radix-16 passes.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int radix_nst(int lg) { return (lg + 3) / 4; }
+__host__ __device__ constexpr int radix_lgr(int lg, int s) {
+  return (lg % 4 != 0 && s == 0) ? (lg % 4) : 4;
+}
+__host__ __device__ constexpr int radix_lgns(int lg, int s) {
+  return s == 0 ? 0 : radix_lgns(lg, s - 1) + radix_lgr(lg, s - 1);
+}
+// Offset (in complex entries) of pass s's twiddle basis in the per-length
+// table.  Pass s with Ns > 1 stores lgr(s) rows of Ns entries:
+//   row e (e = 0..lgr-1), column k:  W_{Ns*R}^{(2^e) * k}.
+__host__ __device__ constexpr int stage_tw_off(int lg, int s) {
+  return s == 0 ? 0
+                : stage_tw_off(lg, s - 1) +
+                      ((radix_lgns(lg, s - 1) > 0) ? radix_lgr(lg, s - 1) * (1 << radix_lgns(lg, s - 1)) : 0);
+}
+__host__ __device__ constexpr int stage_tw_size(int lg) { return stage_tw_off(lg, radix_nst(lg)); }
+
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// Row pad (complex entries) so that the lane groups of one warp that touch
+// different transforms land on disjoint banks (derived from a bank model of
+// every pass's access pattern).
+__host__ __device__ constexpr int tile_group_count(int lg, int C, bool in_cf, bool out_cf, int s) {
+  return (s >= radix_nst(lg))
+             ? 1
+             : cmax(cmin(C, (((s == 0) && in_cf) || ((s == radix_nst(lg) - 1) && out_cf))
+                                  ? cmin(C, 32)
+                                  : (((1 << lg) >> radix_lgr(lg, s)) < 32 ? cmax(1, 32 / ((1 << lg) >> radix_lgr(lg, s))) : 1)),
+                    tile_group_count(lg, C, in_cf, out_cf, s + 1));
+}
+__host__ __device__ constexpr int tile_row_pad(int lg, int C, bool in_cf, bool out_cf) {
+  return ((32 / tile_group_count(lg, C, in_cf, out_cf, 0)) % 16 - (((1 << lg) + ((1 << lg) >> 4)) % 16) + 32) % 16;
+}
+
+template <int LG, int C, bool IN_CF, bool OUT_CF>
+struct TileCfg {
+  static constexpr int L = 1 << LG;
+  static constexpr int P = L < 16 ? L : 16;         // points per thread
+  static constexpr int T = C * L / P;               // threads per CTA
+  static constexpr int NST = radix_nst(LG);
+  static constexpr int LP = L + (L >> 4) + tile_row_pad(LG, C, IN_CF, OUT_CF);
+  static constexpr int SM_TILE = NST > 1 ? C * LP : 0;   // complex entries
+  static constexpr bool EPI = IN_CF && OUT_CF;            // column pass: may carry the four-step twiddle
+  static constexpr int SM_EPI = EPI ? C * 16 : 0;         // four-step per-column step table
+  static constexpr int SMEM_BYTES = (SM_TILE + SM_EPI) * 8;
+};
+
+__device__ __forceinline__ int pidx(int n) { return n + (n >> 4); }
+
+// ---------------------------------------------------------------------------
+// Kernel arguments.  Tile t = (b, g) with b = t / tiles_per_batch and
+// g = t % tiles_per_batch; element (c, n) of the tile lives at
+//   in  + b*in_bstride  + g*in_gstride  + c*in_sc  + n*in_sn
+//   out + b*out_bstride + g*out_gstride + c*out_sc + n*out_sn
+// (all in complex units).  Column index g*C + c >= ncols is skipped (ragged
+// last tile of a batch).
+// ---------------------------------------------------------------------------
+struct TileArgs {
+  const float2* in;
+  float2* out;
+  const float2* tw;  // per-length stage twiddle table (stage_tw_size(LG) entries)
+  long long tiles_per_batch;
+  long long in_bstride, in_gstride, in_sc, in_sn;
+  long long out_bstride, out_gstride, out_sc, out_sn;
+  long long ncols;
+  // Four-step twiddle W_N^{(g*C+c) * k} on the output (k = output index),
+  // N = 2^ft_lgN, from the two-level table W_N^m = lo[m & (2^ft_s-1)] * hi[m >> ft_s].
+  const float2* ft_lo;
+  const float2* ft_hi;
+  int ft_lgN;  // 0: no four-step twiddle
+  int ft_s;
+  int conj_in;      // negate imaginary parts on load
+  int scale_out;    // multiply outputs by (sx, sy) component-wise
+  float sx, sy;
+  int stream_in;    // 1: read with evict-first (.cs) hint; 0: keep in L2 (.cg)
+  int stream_out;   // 1: write with evict-first (.cs) hint
+};
+
+template <int R>
+__device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, int NS, int k) {
+  if constexpr (R >= 2) {
+    float2 w[R];
+    w[1] = __ldg(t + k);
+    if constexpr (R >= 4) w[2] = __ldg(t + NS + k);
+    if constexpr (R >= 8) w[4] = __ldg(t + 2 * NS + k);
+    if constexpr (R >= 16) w[8] = __ldg(t + 3 * NS + k);
+    if constexpr (R >= 4) w[3] = cmul(w[1], w[2]);
+    if constexpr (R >= 8) {
+      w[5] = cmul(w[4], w[1]);
+      w[6] = cmul(w[4], w[2]);
+      w[7] = cmul(w[4], w[3]);
+    }
+    if constexpr (R >= 16) {
+#pragma unroll
+      for (int r = 1; r < 8; ++r) w[8 + r] = cmul(w[8], w[r]);
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+  }
+}
+
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S>
+__device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
+                                           const TileArgs& a, const float2* gin, float2* gout,
+                                           long long col0, const float2* epi_tab) {
+  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
+  constexpr int L = Cfg::L, P = Cfg::P, T = Cfg::T, NST = Cfg::NST, LP = Cfg::LP;
+  constexpr int LGR = radix_lgr(LG, S), R = 1 << LGR;
+  constexpr int LGNS = radix_lgns(LG, S), NS = 1 << LGNS;
+  constexpr bool FIRST = (S == 0), LAST = (S == NST - 1);
+  constexpr bool CF = (FIRST && IN_CF) || (LAST && OUT_CF);
+  constexpr int NB = P / R;   // butterflies per thread in this pass
+  constexpr int LR = L / R;
+  const int tid = threadIdx.x;
+
+  int cc[NB], jj[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    if constexpr (CF) {
+      cc[i] = tid % C;
+      jj[i] = (tid / C) * NB + i;
+    } else {
+      const int b = tid + i * T;
+      cc[i] = b / LR;
+      jj[i] = b % LR;
+    }
+  }
+
+  // ---- gather the R inputs of each butterfly ----
+  if constexpr (FIRST) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const bool ok = (col0 + cc[i]) < a.ncols;
+      const float2* p = gin + cc[i] * a.in_sc + (long long)jj[i] * a.in_sn;
+      const long long step = (long long)LR * a.in_sn;
+      if (a.stream_in) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i * R + r] = ok ? __ldcs(p + r * step) : make_float2(0.f, 0.f);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i * R + r] = ok ? __ldcg(p + r * step) : make_float2(0.f, 0.f);
+      }
+    }
+    if (a.conj_in) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) v[p].y = -v[p].y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i * R + r] = sm[cc[i] * LP + pidx(jj[i] + r * LR)];
+  }
+
+  // ---- twiddles W_{Ns*R}^{r*(j mod Ns)} ----
+  if constexpr (NS > 1) {
+    const float2* t = a.tw + stage_tw_off(LG, S);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) apply_stage_twiddle<R>(v + i * R, t, NS, jj[i] & (NS - 1));
+  }
+
+  // ---- R-point DFT in registers ----
+#pragma unroll
+  for (int i = 0; i < NB; ++i) dft_fwd<R>(v + i * R);
+
+  // ---- scatter outputs ----
+  if constexpr (LAST) {
+    static_assert(NB == 1, "last pass is radix-16 (or the whole length)");
+    // After the last pass NS = L/R and j < NS: output index k = j + q*NS.
+    const int c = cc[0], j = jj[0];
+    const bool ok = (col0 + c) < a.ncols;
+    if (Cfg::EPI && a.ft_lgN) {
+      // four-step twiddle W_N^{n2*k}, n2 = col0 + c, k = j + q*NS
+      //   = W_N^{n2*j} * W_N^{n2*NS*q}; the second factor is the per-column
+      //   table epi_tab[c*16 + q] built at kernel start.
+      const unsigned n2 = (unsigned)(col0 + c);
+      const unsigned m = n2 * (unsigned)j;
+      const unsigned mask = (1u << a.ft_s) - 1u;
+      const float2 base = cmul(__ldg(a.ft_lo + (m & mask)), __ldg(a.ft_hi + (m >> a.ft_s)));
+#pragma unroll
+      for (int q = 0; q < R; ++q) v[q] = cmul(v[q], cmul(base, epi_tab[c * 16 + q]));
+    }
+    if (a.scale_out) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) v[q] = make_float2(v[q].x * a.sx, v[q].y * a.sy);
+    }
+    if (ok) {
+      float2* p = gout + c * a.out_sc + (long long)j * a.out_sn;
+      const long long step = (long long)NS * a.out_sn;
+      if (a.stream_out) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) __stcs(p + q * step, v[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) __stcg(p + q * step, v[q]);
+      }
+    }
+  } else {
+    if constexpr (!FIRST) __syncthreads();   // all reads of this pass are done
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int j = jj[i];
+      const int base = ((j >> LGNS) << (LGNS + LGR)) + (j & (NS - 1));
+#pragma unroll
+      for (int q = 0; q < R; ++q) sm[cc[i] * LP + pidx(base + q * NS)] = v[i * R + q];
+    }
+    __syncthreads();
+    tile_stage<LG, C, IN_CF, OUT_CF, S + 1>(v, sm, a, gin, gout, col0, epi_tab);
+  }
+}
+
+template <int LG, int C, bool IN_CF, bool OUT_CF>
+__global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
+    tile_fft_kernel(const TileArgs a) {
+  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
+  extern __shared__ float2 smem[];
+  float2* sm = smem;
+  float2* epi_tab = smem + Cfg::SM_TILE;
+
+  const long long tile = (long long)blockIdx.x;
+  const long long b = tile / a.tiles_per_batch;
+  const long long g = tile - b * a.tiles_per_batch;
+  const long long col0 = g * C;
+  const float2* gin = a.in + b * a.in_bstride + g * a.in_gstride;
+  float2* gout = a.out + b * a.out_bstride + g * a.out_gstride;
+
+  if (Cfg::EPI && a.ft_lgN) {
+    // per-column step factors W_N^{n2*NS_last*q}, q = 0..15
+    constexpr int NS_LAST = 1 << radix_lgns(LG, Cfg::NST - 1);
+    for (int e = threadIdx.x; e < C * 16; e += Cfg::T) {
+      const int c = e >> 4, q = e & 15;
+      const unsigned m = (unsigned)(col0 + c) * (unsigned)NS_LAST * (unsigned)q;
+      const unsigned mm = m & ((1u << a.ft_lgN) - 1u);
+      const unsigned mask = (1u << a.ft_s) - 1u;
+      epi_tab[e] = cmul(__ldg(a.ft_lo + (mm & mask)), __ldg(a.ft_hi + (mm >> a.ft_s)));
+    }
+    if constexpr (Cfg::NST == 1) __syncthreads();
+  }
+
+  float2 v[Cfg::P];
+  tile_stage<LG, C, IN_CF, OUT_CF, 0>(v, sm, a, gin, gout, col0, epi_tab);
+}
+
+}  // namespace gbfft

@@ -1,0 +1,40 @@
+// tile_registry.h -- lookup of the compiled tile-FFT kernel variants.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "tile_fft.cuh"
+
+namespace gbfft {
+
+// Thread mappings of the first / last pass (see tile_fft.cuh):
+//   MAP_JJ: contiguous transforms in, contiguous out (batched single pass, 2-D rows)
+//   MAP_CC: adjacent columns in and out (four-step column pass, 2-D columns)
+//   MAP_JC: contiguous rows in, adjacent columns out (four-step row pass)
+enum TileMap { MAP_JJ = 0, MAP_CC = 1, MAP_JC = 2 };
+
+struct TileKernelInfo {
+  const void* fn;   // __global__ void(TileArgs)
+  int threads;      // CTA size
+  int smem_bytes;   // dynamic shared memory
+  int lg, C, map;
+};
+
+// Columns per CTA the JJ variant is compiled with for length 2^lg.
+constexpr int jj_cols(int lg) { return lg >= 12 ? 1 : (lg >= 4 ? (4096 >> lg) : 256); }
+
+// Returns NULL when (map, lg, C) was not compiled.
+const TileKernelInfo* tile_kernel(int map, int lg, int C);
+
+// per-file tables (tile_inst_*.cu)
+const TileKernelInfo* tile_kernel_jj(int lg);
+const TileKernelInfo* tile_kernel_cc_a(int lg, int C);
+const TileKernelInfo* tile_kernel_cc_b(int lg, int C);
+const TileKernelInfo* tile_kernel_cc_c(int lg, int C);
+const TileKernelInfo* tile_kernel_jc_a(int lg, int C);
+const TileKernelInfo* tile_kernel_jc_b(int lg, int C);
+
+#define GBFFT_TK(LG, C, ICF, OCF, MAP)                                                         \
+  {(const void*)&tile_fft_kernel<LG, C, ICF, OCF>, TileCfg<LG, C, ICF, OCF>::T,                 \
+   TileCfg<LG, C, ICF, OCF>::SMEM_BYTES, LG, C, MAP}
+
+}  // namespace gbfft

@@ -1,0 +1,61 @@
+// twiddle.cu -- device-side generation of the twiddle look-up tables
+// (paper Sec. 2.3.1: the sine/cosine values are computed once, before the FFT,
+// and kept in a table the butterflies read).  Every entry is evaluated in FP64
+// with sincospi on an exactly representable argument -2m/M (M a power of two,
+// the exponent m reduced mod M by Eq. 3) and rounded once to FP32.
+#include <cuda_runtime.h>
+
+#include "gbfft_internal.h"
+#include "tile_fft.cuh"
+
+namespace gbfft {
+
+__device__ __forceinline__ float2 w_entry(long long m, long long M) {
+  m %= M;
+  double s, c;
+  sincospi(-2.0 * (double)m / (double)M, &s, &c);
+  return make_float2((float)c, (float)s);
+}
+
+// Stage table of length L = 2^lg: for pass s with Ns > 1, row e, column k
+// holds W_{Ns*R}^{2^e * k} at stage_tw_off(lg, s) + e*Ns + k.
+__global__ void gen_stage_twiddles(float2* tab, int lg) {
+  const int total = stage_tw_size(lg);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int s = 1;
+    while (s + 1 < radix_nst(lg) && idx >= stage_tw_off(lg, s + 1)) ++s;
+    const int local = idx - stage_tw_off(lg, s);
+    const int lgns = radix_lgns(lg, s), lgr = radix_lgr(lg, s);
+    const int NS = 1 << lgns;
+    const int e = local / NS, k = local % NS;
+    const long long M = 1LL << (lgns + lgr);
+    tab[idx] = w_entry((1LL << e) * (long long)k, M);
+  }
+}
+
+// tab[i] = W_N^{i * step}, i < count, N = 2^lgN.
+__global__ void gen_power_twiddles(float2* tab, int lgN, long long count, long long step) {
+  const long long N = 1LL << lgN;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    tab[i] = w_entry((i * step) % N, N);
+}
+
+cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s) {
+  const int total = stage_tw_size(lg);
+  if (total == 0) return cudaSuccess;
+  const int threads = 256;
+  const int blocks = (total + threads - 1) / threads;
+  gen_stage_twiddles<<<blocks, threads, 0, s>>>(tab, lg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const int threads = 256;
+  const long long blocks = (count + threads - 1) / threads;
+  gen_power_twiddles<<<(unsigned)(blocks < 4096 ? blocks : 4096), threads, 0, s>>>(tab, lgN, count, step);
+  return cudaGetLastError();
+}
+
+}  // namespace gbfft

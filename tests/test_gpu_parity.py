@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded complex64 inputs.
+
+Bar: relative L2 error of every transform <= 5e-7 * log2(N) for the FP32
+path (the stated FP32 tolerance; an FP32 radix-16 FFT has an RMS error of a
+few 1e-8 * sqrt(log2 N), so this leaves a wide margin while still catching a
+wrong twiddle, which costs O(1)).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1707_07263_gb300 import _lib, workloads
+
+pytestmark = pytest.mark.gpu
+
+DIRS = {"fwd": 0, "inv": 1, "adj": 2, "adj_inv": 3}
+
+
+def tol32(n: int) -> float:
+    return 5e-7 * max(1.0, np.log2(n))
+
+
+def oracle_dir(x: np.ndarray, d: int) -> np.ndarray:
+    """Oracle for every direction code of the ABI."""
+    x = x.astype(np.complex128)
+    n = x.shape[-1]
+    if d == 0:
+        return oracle.transform(x, oracle.FORWARD)
+    if d == 1:
+        return oracle.transform(x, oracle.INVERSE)
+    if d == 2:
+        return oracle.transform(x, oracle.ADJOINT)
+    return oracle.transform(x, oracle.FORWARD) / n   # adjoint of the inverse
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load()
+
+
+class CPlan:
+    """Minimal plan wrapper straight over the C ABI (no autograd layer)."""
+
+    def __init__(self, lib, h):
+        assert h, _lib.ERRORS.get(lib.fft_last_error())
+        self.lib, self.h = lib, ctypes.c_void_p(h)
+        ws = lib.fft_plan_workspace_bytes(self.h)
+        self.ws = None
+        if ws:
+            self.ws = torch.empty(ws, dtype=torch.uint8, device="cuda")
+            assert lib.fft_plan_set_workspace(self.h, ctypes.c_void_p(self.ws.data_ptr())) == 0
+
+    def run(self, x: torch.Tensor, d: int, out=None) -> torch.Tensor:
+        out = torch.empty_like(x) if out is None else out
+        s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        rc = self.lib.fft_exec_dir(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), d, s)
+        assert rc == 0, _lib.ERRORS.get(rc, rc)
+        return out
+
+    def __del__(self):
+        self.lib.fft_destroy(self.h)
+
+
+def run_1d(lib, x: np.ndarray, d: int, inplace=False) -> np.ndarray:
+    batch, n = x.shape
+    p = CPlan(lib, lib.fft_plan_create(n, batch, d, 0))
+    xt = torch.from_numpy(x).cuda()
+    out = p.run(xt, d, out=xt if inplace else None)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def assert_rows(got, ref, tol, what):
+    errs = oracle.rel_l2_rows(got, ref)
+    assert np.all(np.isfinite(got)), f"{what}: non-finite output"
+    assert errs.max() <= tol, f"{what}: max rel-L2 {errs.max():.3e} > {tol:.2e} (row {errs.argmax()})"
+
+
+# --- single on-chip pass: every length 2^1..2^14, ragged batches -----------------
+@pytest.mark.parametrize("lg", range(1, 15))
+@pytest.mark.parametrize("batch", [1, 3, 37])
+def test_single_pass_forward(lib, lg, batch):
+    n = 1 << lg
+    x = workloads.cgauss(n, batch, seed=1000 + lg * 7 + batch)
+    got = run_1d(lib, x, 0)
+    assert_rows(got, oracle_dir(x, 0), tol32(n), f"fwd N={n} batch={batch}")
+
+
+@pytest.mark.parametrize("lg", [1, 2, 3, 4, 5, 7, 10, 12, 13, 14])
+@pytest.mark.parametrize("d", ["inv", "adj", "adj_inv"])
+def test_single_pass_directions(lib, lg, d):
+    n = 1 << lg
+    x = workloads.uniform(n, 5, seed=2000 + lg)
+    got = run_1d(lib, x, DIRS[d])
+    assert_rows(got, oracle_dir(x, DIRS[d]), tol32(n), f"{d} N={n}")
+
+
+def test_single_pass_in_place(lib):
+    x = workloads.cgauss(1024, 9, seed=77)
+    got = run_1d(lib, x, 0, inplace=True)
+    assert_rows(got, oracle_dir(x, 0), tol32(1024), "in-place N=1024")
+
+
+def test_config1_round_trip(lib):
+    """N=4096, batch 1, U[-1,1]: forward against the O(N^2) DFT and the
+    inverse round trip."""
+    n = 4096
+    x = workloads.uniform(n, 1, workloads.seed_for(0))
+    X = run_1d(lib, x, 0)
+    ref = oracle.dft(x.astype(np.complex128))
+    assert oracle.rel_l2(X, ref) <= tol32(n)
+    back = run_1d(lib, X.astype(np.complex64), 1)
+    assert oracle.rel_l2(back, x) <= 2 * tol32(n)
+
+
+# --- four-step: 2^15 .. 2^22 at small batch --------------------------------------
+@pytest.mark.parametrize("lg", [15, 16, 17, 18, 20, 22])
+def test_fourstep_forward(lib, lg):
+    n = 1 << lg
+    batch = 2 if lg <= 18 else 1
+    x = workloads.cgauss(n, batch, seed=3000 + lg)
+    got = run_1d(lib, x, 0)
+    assert_rows(got, oracle_dir(x, 0), tol32(n), f"four-step fwd N=2^{lg}")
+
+
+@pytest.mark.parametrize("lg", [15, 19])
+@pytest.mark.parametrize("d", ["inv", "adj", "adj_inv"])
+def test_fourstep_directions(lib, lg, d):
+    n = 1 << lg
+    x = workloads.uniform(n, 1, seed=4000 + lg)
+    got = run_1d(lib, x, DIRS[d])
+    assert_rows(got, oracle_dir(x, DIRS[d]), tol32(n), f"four-step {d} N=2^{lg}")
+
+
+def test_fourstep_in_place(lib):
+    n = 1 << 16
+    x = workloads.cgauss(n, 3, seed=99)
+    got = run_1d(lib, x, 0, inplace=True)
+    assert_rows(got, oracle_dir(x, 0), tol32(n), "four-step in place")
+
+
+@pytest.mark.parametrize("split", [7, 9, 12])
+def test_fourstep_other_splits(lib, monkeypatch, split):
+    """The same transform through different N1 x N2 splits."""
+    monkeypatch.setenv("GBFFT_FORCE_SPLIT", str(split))
+    n = 1 << 20
+    x = workloads.cgauss(n, 1, seed=5000 + split)
+    got = run_1d(lib, x, 0)
+    assert_rows(got, oracle_dir(x, 0), tol32(n), f"split 2^{split} x 2^{20 - split}")
+
+
+# --- full-size large transforms (config 3a) ----------------------------------------
+@pytest.mark.parametrize("lg", [24, 26])
+def test_fourstep_full_size(lib, lg):
+    n = 1 << lg
+    x = workloads.uniform(n, 1, workloads.seed_for(2))
+    got = run_1d(lib, x, 0)
+    ref = oracle.fft(x.astype(np.complex128))
+    assert_rows(got, ref, tol32(n), f"N=2^{lg}")
+
+
+# --- 2-D -----------------------------------------------------------------------
+def run_2d(lib, x: np.ndarray, d: int) -> np.ndarray:
+    batch, ny, nx = x.shape
+    p = CPlan(lib, lib.fft_plan_create_2d(ny, nx, batch, d, 0))
+    xt = torch.from_numpy(x).cuda()
+    out = p.run(xt, d)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("ny,nx,batch", [(2, 2, 1), (8, 32, 2), (64, 16, 1), (256, 512, 1), (32, 4096, 1),
+                                         (4096, 64, 1), (1024, 1024, 1)])
+@pytest.mark.parametrize("d", ["fwd", "inv"])
+def test_2d(lib, ny, nx, batch, d):
+    x = workloads.cgauss(ny * nx, batch, seed=ny * 31 + nx).reshape(batch, ny, nx)
+    got = run_2d(lib, x, DIRS[d])
+    ref = oracle.fft2(x.astype(np.complex128), oracle.FORWARD if d == "fwd" else oracle.INVERSE)
+    tol = tol32(ny * nx)
+    for b in range(batch):
+        assert oracle.rel_l2(got[b], ref[b]) <= tol, f"2-D {ny}x{nx} {d}"
+
+
+def test_2d_sar_full_size(lib):
+    """8192 x 8192 speckle + 64 scatterers of amplitude 100 (config 3b)."""
+    x = workloads.sar_image(8192, 8192, seed=workloads.seed_for(2, 1))
+    got = run_2d(lib, x[None], 0)[0]
+    ref = oracle.fft2(x.astype(np.complex128))
+    assert oracle.rel_l2(got, ref) <= tol32(8192 * 8192)
+
+
+# --- error paths that need a device pointer ---------------------------------------
+def test_misaligned_pointer_rejected(lib):
+    p = CPlan(lib, lib.fft_plan_create(64, 1, 0, 0))
+    buf = torch.zeros(200, dtype=torch.uint8, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.fft_exec(p.h, ctypes.c_void_p(buf.data_ptr() + 4), ctypes.c_void_p(buf.data_ptr() + 4), s)
+    assert rc == -2
+
+
+def test_missing_workspace(lib):
+    h = ctypes.c_void_p(lib.fft_plan_create(1 << 16, 1, 0, 0))
+    assert lib.fft_plan_workspace_bytes(h) == (1 << 16) * 8
+    x = torch.zeros(1 << 16, dtype=torch.complex64, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.fft_exec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), s) == -3
+    assert lib.fft_plan_set_workspace(h, None) == 0       # library-owned workspace
+    assert lib.fft_exec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), s) == 0
+    lib.fft_destroy(h)
