@@ -1,0 +1,493 @@
+"""Benchmark: batched 1-D complex64 FFTs on GB300 through libgbfft.
+
+Default workload (one "step"): for each N in {2^10, 2^12, 2^14}, a forward and
+an inverse transform of batch = 2^26 / N transforms (2^26 complex64 points,
+512 MiB per direction, larger than the 126 MB L2, so no L2 flush is needed
+between launches), inputs CN(0,1) from a fixed seed.  Metric: GFLOP/s with
+the conventional 5 N log2 N flops per complex transform.
+
+Also printed on the same JSON line:
+  roofline      the dominant kernel's algorithmic HBM bytes (16 B per point:
+                one complex64 read + one write) / its CUDA-event launch time,
+                against the measured copy bandwidth;
+  cpu_baseline  the FP64 oracle (test infrastructure) timed on the host cores
+                on a bounded sample of the same workload;
+  e2e           the same metric through the public API with pinned HOST
+                buffers, host->device and device->host copies inside the
+                timed region;
+  clocks        nvidia-smi samples taken during the timed region.
+
+``--impl reference`` times the oracle instead (the deliberately slow CPU
+baseline) and prints the same line with "impl": "reference".
+Other workloads for measurement only: --workload large | 2d | tc | many | cfg1.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TOTAL = 1 << 26
+HBM_FALLBACK = 6800.0
+METRIC = "GFLOP/s (5N log2N) and % of HBM roofline per FFT size; split-TC vs plain FP32 at stated err"
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", HBM_FALLBACK)), "measured"
+    return HBM_FALLBACK, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1707_07263_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch of `kernel_key` from the committed ncu summary, or
+    None when the kernels changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != source_hash():
+        return None
+    e = d.get("kernels", {}).get(kernel_key)
+    return None if e is None else float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+# ------------------------------------------------------------------------------------
+# workloads
+# ------------------------------------------------------------------------------------
+def workload_cfg2():
+    """(name, list of (label, n, batch, dir)) for the default step."""
+    items = []
+    for lg in (10, 12, 14):
+        n = 1 << lg
+        items.append((f"fwd_2^{lg}", n, TOTAL // n, 0))
+        items.append((f"inv_2^{lg}", n, TOTAL // n, 1))
+    desc = ("batched 1D complex64 FFT, N in {2^10, 2^12, 2^14}, batch = 2^26/N, CN(0,1) inputs, "
+            "forward + inverse per size (single-kernel on-chip path, FP32)")
+    return desc, items
+
+
+def workload_large():
+    items = [("fwd_2^24", 1 << 24, 1, 0), ("fwd_2^26", 1 << 26, 1, 0)]
+    return "1D complex64 FFT via the four-step split, N = 2^24 and 2^26, batch 1, U[-1,1]", items
+
+
+def flops(n, batch):
+    return 5.0 * n * np.log2(n) * batch
+
+
+# ------------------------------------------------------------------------------------
+# CPU baseline (oracle)
+# ------------------------------------------------------------------------------------
+def oracle_sample(items, budget_s: float):
+    """Time the FP64 oracle on a bounded sample: for each (n, dir) item, as many
+    whole transforms as fit the per-item share of the budget (at least one)."""
+    import oracle
+    from paper_1707_07263_gb300 import workloads
+    oracle.build()
+    share = budget_s / max(1, len(items))
+    total_flop, total_t, desc = 0.0, 0.0, []
+    for label, n, batch, d in items:
+        x = workloads.cgauss(n, 1, seed=7).astype(np.complex128)
+        rows, t = 0, 0.0
+        while rows < batch and (t < share or rows == 0):
+            t0 = time.perf_counter()
+            oracle.fft(x, oracle.FORWARD if d == 0 else oracle.INVERSE)
+            t += time.perf_counter() - t0
+            rows += 1
+        total_flop += flops(n, rows)
+        total_t += t
+        desc.append(f"{rows}x{label}")
+    return total_flop / total_t / 1e9, ", ".join(desc), total_t
+
+
+# ------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    from paper_1707_07263_gb300 import _lib
+    from paper_1707_07263_gb300 import workloads
+
+    world, rank, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+
+    if args.workload == "cfg2":
+        desc, items = workload_cfg2()
+    elif args.workload == "large":
+        desc, items = workload_large()
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+
+    stream = torch.cuda.Stream(device=dev)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+
+    # one plan per (n, batch); inputs resident in HBM before timing
+    plans, bufs = {}, {}
+    for label, n, batch, d in items:
+        key = (n, batch)
+        if key not in plans:
+            h = lib.fft_plan_create(n, batch, 0, 0)
+            if not h:
+                raise RuntimeError(f"plan {n}x{batch}: {_lib.ERRORS.get(lib.fft_last_error())}")
+            h = ctypes.c_void_p(h)
+            ws = lib.fft_plan_workspace_bytes(h)
+            wsbuf = torch.empty(ws, dtype=torch.uint8, device=dev) if ws else None
+            if ws:
+                _lib.check(lib.fft_plan_set_workspace(h, ctypes.c_void_p(wsbuf.data_ptr())))
+            plans[key] = (h, wsbuf)
+    maxel = max(n * b for _, n, b, _ in items)
+    x_host = workloads.cgauss(maxel, 1, seed=workloads.seed_for(1) + rank).reshape(-1)
+    xin = torch.from_numpy(x_host).to(dev)
+    xout = torch.empty_like(xin)
+    launches_per_step = sum(lib.fft_plan_launches(plans[(n, b)][0]) for _, n, b, _ in items)
+
+    def exec_item(i, src, dst):
+        label, n, batch, d = items[i]
+        rc = lib.fft_exec_dir(plans[(n, batch)][0], ctypes.c_void_p(src.data_ptr()),
+                              ctypes.c_void_p(dst.data_ptr()), d, sh)
+        if rc:
+            raise RuntimeError(f"exec {label}: {_lib.ERRORS.get(rc)}")
+
+    def one_step(ev=None):
+        for i in range(len(items)):
+            if ev is not None:
+                ev[i][0].record(stream)
+            exec_item(i, xin, xout)
+            if ev is not None:
+                ev[i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in items]
+           for _ in range(K)]
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0e.record(stream)
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                one_step(evs[k])
+        t1e.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = t0e.elapsed_time(t1e)
+    per_item_ms = [float(np.mean([evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(K)]))
+                   for i in range(len(items))]
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / K
+    step_flop = sum(flops(n, b) for _, n, b, _ in items)
+    value = step_flop * world / (ms_step * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel ----
+    peak, peak_kind = measured_peaks()
+    dom = int(np.argmax(per_item_ms))
+    label, n, batch, d = items[dom]
+    nl = lib.fft_plan_launches(plans[(n, batch)][0])
+    # each launch of every plan kind reads and writes the whole array once
+    bytes_launch = 16.0 * n * batch
+    # average per-launch duration of the dominant plan's kernels
+    achieved = bytes_launch / (per_item_ms[dom] / nl * 1e-3) / 1e9
+    lg = int(np.log2(n))
+    traffic = ncu_traffic(f"tile_fft_jj_lg{lg}") if nl == 1 else None
+    per_size = {}
+    for i, (lab, nn, bb, dd) in enumerate(items):
+        gbs = 16.0 * nn * bb / (per_item_ms[i] * 1e-3) / 1e9
+        per_size[lab] = {"us": round(per_item_ms[i] * 1e3, 2),
+                         "gflops": round(flops(nn, bb) / (per_item_ms[i] * 1e-3) / 1e9, 1),
+                         "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
+
+    # ---- end to end through the public API with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        from paper_1707_07263_gb300 import api
+        host_in = torch.from_numpy(x_host).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        dx = torch.empty_like(xin)
+        dy = torch.empty_like(xin)
+        h2d = d2h = 0
+
+        def e2e_step():
+            nonlocal h2d, d2h
+            h2d = d2h = 0
+            with torch.cuda.stream(stream):
+                for i, (lab, nn, bb, dd) in enumerate(items):
+                    m = nn * bb
+                    dx[:m].copy_(host_in[:m], non_blocking=True)
+                    h2d += m * 8
+                    p = api.get_plan("1d", (nn,), bb, "fp32", dev)
+                    p.exec_ptr(dx.data_ptr(), dy.data_ptr(), dd, stream)
+                    host_out[:m].copy_(dy[:m], non_blocking=True)
+                    d2h += m * 8
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            e2e_step()
+        torch.cuda.synchronize()
+        ke = max(1, min(K, 5))
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a0.elapsed_time(a1) / ke
+        if dist:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": round(step_flop * world / (e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+               "ms_per_step": round(e_ms, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "api": "paper_1707_07263_gb300.api.Plan.exec_ptr -> fft_exec_dir, pinned host tensors"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, sample, secs = oracle_sample(items, args.cpu_budget)
+        cpu = {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 recursive radix-2 oracle, 1 thread, {sample} ({secs:.1f} s)"}
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GFLOP/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": desc, "points_per_transform_batch": TOTAL, "sizes": [n for _, n, _, _ in items],
+                   "l2": "inputs and outputs (512 MiB each) larger than L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": f"tile_fft_kernel (JJ, L=2^{lg}, {label})",
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"},
+        "per_size": per_size,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches_per_step * K),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ------------------------------------------------------------------------------------
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    desc, items = workload_cfg2() if args.workload == "cfg2" else workload_large()
+    import oracle
+    from paper_1707_07263_gb300 import workloads
+    oracle.build()
+    # one step = one transform of each (size, direction) item: a bounded sample
+    xs = {n: workloads.cgauss(n, 1, seed=workloads.seed_for(1)).astype(np.complex128) for _, n, _, _ in items}
+
+    def step():
+        for _, n, _, d in items:
+            oracle.fft(xs[n], oracle.FORWARD if d == 0 else oracle.INVERSE)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    secs = time.perf_counter() - t0
+    step_flop = sum(flops(n, 1) for _, n, _, _ in items)
+    ms = secs / args.steps * 1e3
+    v = step_flop / (ms * 1e-3) / 1e9
+    sample = "one transform per (size, direction) per step: " + ", ".join(l for l, _, _, _ in items)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sizes": [n for _, n, _, _ in items]},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_case(args):
+    """One plan (2^lg points, batch 2^26/2^lg unless --batch) run warmup + iters
+    times: the small, self-contained case used for ncu captures."""
+    import torch
+    from paper_1707_07263_gb300 import _lib
+    lib = _lib.load()
+    n = 1 << args.case
+    batch = args.batch or max(1, TOTAL // n)
+    h = lib.fft_plan_create(n, batch, args.dir, args.prec)
+    if not h:
+        raise RuntimeError(_lib.ERRORS.get(lib.fft_last_error()))
+    h = ctypes.c_void_p(h)
+    ws = lib.fft_plan_workspace_bytes(h)
+    wsb = torch.empty(ws, dtype=torch.uint8, device="cuda") if ws else None
+    if ws:
+        _lib.check(lib.fft_plan_set_workspace(h, ctypes.c_void_p(wsb.data_ptr())))
+    x = torch.randn(n * batch, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(args.warmup):
+        _lib.check(lib.fft_exec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), s))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        _lib.check(lib.fft_exec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), s))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    buf = ctypes.create_string_buffer(512)
+    lib.fft_plan_describe(h, buf, 512)
+    print(json.dumps({"case": f"2^{args.case} x {batch}", "us": round(ms * 1e3, 2),
+                      "hbm_gbs_per_launch": round(16.0 * n * batch * lib.fft_plan_launches(h) / (ms * 1e-3) / 1e9, 1),
+                      "plan": buf.value.decode()}))
+    lib.fft_destroy(h)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", type=int, default=0, help="run one plan of 2^CASE points (profiling case)")
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--dir", type=int, default=0)
+    ap.add_argument("--prec", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -152,8 +152,8 @@ def rel_l2(got, ref) -> float:
     """||got - ref||_2 / ||ref||_2 over all elements, in FP64."""
     g = np.asarray(got, dtype=np.complex128)
     r = np.asarray(ref, dtype=np.complex128)
-    den = np.sqrt(np.sum(np.abs(r) ** 2))
-    num = np.sqrt(np.sum(np.abs(g - r) ** 2))
+    den = np.linalg.norm(r.reshape(-1))
+    num = np.linalg.norm((g - r).reshape(-1))
     return float(num / den) if den > 0 else float(num)
 
 

@@ -33,6 +33,8 @@ struct fft_plan {
   int c1, c2;  // transforms per CTA of the first / second pass
   const gbfft::TileKernelInfo* k1;
   const gbfft::TileKernelInfo* k2;
+  const gbfft::TileKernelInfo* ktma;  // persistent TMA-staged single-pass kernel (or NULL)
+  long long tma_grid;                 // its resident-CTA grid
 
   // all twiddle tables live in one device allocation
   void* d_tables;

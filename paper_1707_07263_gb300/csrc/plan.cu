@@ -182,6 +182,25 @@ static void set_out_xf(TileArgs& a, const DirXf& x) {
 // ---- single on-chip pass -------------------------------------------------
 static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
   const DirXf x = dir_xf(dir, p->n);
+  if (p->ktma && ((uintptr_t)in & 15) == 0) {
+    // persistent TMA-staged kernel: grid = resident CTAs, tiles looped
+    TileArgs a;
+    base_args(a);
+    const int C = p->ktma->C;
+    a.in = in;
+    a.out = out;
+    a.tw = p->tw1;
+    a.ncols = p->batch;
+    a.conj_in = x.conj;
+    set_out_xf(a, x);
+    long long ntiles = (p->batch + C - 1) / C;
+    long long grid = p->tma_grid < ntiles ? p->tma_grid : ntiles;
+    int* st = p->d_status;
+    void* args[] = {(void*)&a, (void*)&ntiles, (void*)&st};
+    cudaError_t e = cudaLaunchKernel(p->ktma->fn, dim3((unsigned)grid), dim3(p->ktma->threads), args,
+                                     (size_t)p->ktma->smem_bytes, s);
+    return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
+  }
   TileArgs a;
   base_args(a);
   const int C = p->k1->C;
@@ -314,6 +333,21 @@ static int plan_1d(fft_plan* p, int lgN) {
     p->launches = 1;
     int rc = prepare_kernel(p->k1);
     if (rc) return rc;
+    // Persistent TMA staging pays where several CTAs share an SM and the tile
+    // is large enough to amortise the copy (measured: 2^9..2^12).
+    if (lgN >= 9 && lgN <= 12 && !env_int("GBFFT_NO_TMA", 0)) {
+      p->ktma = tile_kernel_tma(lgN);
+      rc = prepare_kernel(p->ktma);
+      if (rc) return rc;
+      int per_sm = 0, sms = 0, dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->ktma->fn, p->ktma->threads,
+                                                        (size_t)p->ktma->smem_bytes) != cudaSuccess ||
+          per_sm < 1)
+        return FFT_ERR_CUDA;
+      p->tma_grid = (long long)per_sm * sms;
+    }
     return build_tables(p, lgN, 0, 0);
   }
   p->kind = KIND_FOURSTEP;
@@ -487,10 +521,10 @@ int fft_plan_describe(const fft_plan* p, char* buf, size_t len) {
   static const char* kinds[] = {"single", "fourstep", "2d", "many"};
   snprintf(buf, len,
            "kind=%s n=%lld batch=%lld lg1=%d lg2=%d c1=%d c2=%d threads1=%d smem1=%d threads2=%d smem2=%d "
-           "prec=%d launches=%d ws=%zu",
+           "prec=%d launches=%d ws=%zu tma_grid=%lld",
            kinds[p->kind & 3], (long long)p->n, (long long)p->batch, p->lg1, p->lg2, p->c1, p->c2,
            p->k1 ? p->k1->threads : 0, p->k1 ? p->k1->smem_bytes : 0, p->k2 ? p->k2->threads : 0,
-           p->k2 ? p->k2->smem_bytes : 0, p->prec, p->launches, p->ws_bytes);
+           p->k2 ? p->k2->smem_bytes : 0, p->prec, p->launches, p->ws_bytes, p->ktma ? p->tma_grid : 0LL);
   return FFT_OK;
 }
 

@@ -22,6 +22,11 @@ struct TileKernelInfo {
 // Columns per CTA the JJ variant is compiled with for length 2^lg.
 constexpr int jj_cols(int lg) { return lg >= 12 ? 1 : (lg >= 4 ? (4096 >> lg) : 256); }
 
+// Persistent TMA-staged variant of MAP_JJ (tile_fft_tma.cuh), one per length;
+// kernel signature void(TileArgs, long long ntiles, int* status).
+const TileKernelInfo* tile_kernel_tma(int lg);
+constexpr int tma_exchange_width(int lg) { return lg >= 13 ? 4 : 8; }
+
 // Returns NULL when (map, lg, C) was not compiled.
 const TileKernelInfo* tile_kernel(int map, int lg, int C);
 

@@ -101,6 +101,33 @@ def test_single_pass_directions(lib, lg, d):
     assert_rows(got, oracle_dir(x, DIRS[d]), tol32(n), f"{d} N={n}")
 
 
+@pytest.mark.parametrize("lg", [3, 8, 10, 12, 13, 14])
+def test_single_pass_register_path(lib, monkeypatch, lg):
+    """The non-persistent kernel (no TMA staging) gives the same result."""
+    monkeypatch.setenv("GBFFT_NO_TMA", "1")
+    n = 1 << lg
+    x = workloads.cgauss(n, 11, seed=6000 + lg)
+    got = run_1d(lib, x, 1)
+    assert_rows(got, oracle_dir(x, 1), tol32(n), f"register path N={n}")
+
+
+@pytest.mark.parametrize("lg", [6, 10, 12])
+def test_single_pass_8byte_aligned_input(lib, lg):
+    """An input that is 8- but not 16-byte aligned takes the register path."""
+    n = 1 << lg
+    batch = 5
+    x = workloads.cgauss(n, batch, seed=6100 + lg)
+    p = CPlan(lib, lib.fft_plan_create(n, batch, 0, 0))
+    buf = torch.zeros(n * batch + 1, dtype=torch.complex64, device="cuda")
+    src = buf[1:]
+    src.copy_(torch.from_numpy(x.reshape(-1)))
+    assert src.data_ptr() % 16 == 8
+    out = p.run(src, 0)
+    torch.cuda.synchronize()
+    assert_rows(out.cpu().numpy().reshape(batch, n), oracle_dir(x, 0), tol32(n), "8-byte aligned")
+    assert p.lib.fft_status(p.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+
+
 def test_single_pass_in_place(lib):
     x = workloads.cgauss(1024, 9, seed=77)
     got = run_1d(lib, x, 0, inplace=True)
