@@ -127,6 +127,23 @@ GBFFT_API int fft_plan_describe(const fft_plan* plan, char* buf, size_t len);
  * wait gave up).  Synchronises `stream` to read it. */
 GBFFT_API int fft_status(fft_plan* plan, void* stream);
 
+/* Allocation-free four-step transform, for callers that cannot allocate device
+ * memory when they need a transform (inside an allocator or memory-pool
+ * callback, in a plug-in whose host owns all device memory, on real-time paths
+ * that allow allocation only at start-up).  The paper has no counterpart; it
+ * computes what fft_exec_dir computes on a four-step plan of (n, batch).
+ *   n:      power of two, 2^15 <= n <= 2^22;  batch >= 1 and n*batch <= 2^22,
+ *           anything larger returns FFT_ERR_INVALID_ARG without launching.
+ *   dir:    as fft_exec_dir.  in/out: caller-owned device pointers (8-byte
+ *           aligned, in == out allowed).  stream: cudaStream_t or NULL.
+ * Nothing is allocated: the workspace (32 MiB) and the twiddle tables live in a
+ * static device array inside the library, reserved on every GPU that loads it
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (and raises the kernels' shared-memory limit) once; make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU race on it, so serialise them. */
+GBFFT_API int fft_exec_noalloc(int64_t n, int64_t batch, int dir, const void* in, void* out, void* stream);
+
 /* Code of the last failing call on this host thread (FFT_OK if none). */
 GBFFT_API int fft_last_error(void);
 /* Static description of an error code. */

@@ -43,6 +43,7 @@ SIGNATURES = {
     "fft_plan_kind": (_int, [_vp]),
     "fft_plan_describe": (_int, [_vp, ctypes.c_char_p, _sz]),
     "fft_status": (_int, [_vp, _vp]),
+    "fft_exec_noalloc": (_int, [_i64, _i64, _int, _vp, _vp, _vp]),
     "fft_last_error": (_int, []),
     "fft_error_string": (ctypes.c_char_p, [_int]),
 }
