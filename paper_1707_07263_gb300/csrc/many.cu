@@ -1,9 +1,428 @@
-// many.cu -- uneven-length batches (placeholder until the persistent kernel lands).
+// many.cu -- transforms of uneven power-of-two lengths (2^1..2^16), packed back
+// to back, in ONE persistent launch.
+//
+// The plan turns the batch into a queue of tile work items, each sized for a
+// 256-thread CTA (at most 4096 points):
+//   kind 0  batch tile: up to C = 4096/L transforms of the same length L <= 2^12,
+//           each found through a per-column offset (the transforms need not
+//           be adjacent);
+//   kind 1  four-step column tile (C columns of length N1, with the W_N^{n2*k1}
+//           twiddle) of a transform with 2^13 <= N <= 2^16;
+//   kind 2  four-step row tile of such a transform, written transposed.
+// Queue order: every kind-1 tile (largest transforms first), then the batch
+// tiles (largest first), then every kind-2 tile.  CTAs pop items with one
+// atomicAdd on a queue head.  A kind-2 tile waits until all kind-1 tiles of
+// its transform have been written (a per-transform completion counter); since
+// those were dequeued earlier by CTAs that never wait, the wait always ends --
+// it is still bounded (clock64 budget) and a timeout sets FFT_ERR_TIMEOUT in
+// the plan's status word instead of hanging.  The queue head and counters are
+// cleared by a memset issued with every exec, so exec can be captured into a
+// CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
 #include "gbfft_internal.h"
+#include "tile_fft.cuh"
 
 namespace gbfft {
-struct ManyPlan {};
-int many_plan_init(fft_plan*, const int64_t*, int64_t) { return FFT_ERR_UNSUPPORTED; }
-void many_plan_free(fft_plan* p) { delete p->many; p->many = nullptr; }
-int many_exec(fft_plan*, const float2*, float2*, int, cudaStream_t) { return FFT_ERR_UNSUPPORTED; }
+
+struct ManyItem {
+  int kind;   // 0 batch tile, 1 four-step column tile, 2 four-step row tile
+  int lg;     // tile transform length (log2)
+  int ncols;  // valid columns of the tile
+  int tr;     // kind 0: first slot in the offset table; kinds 1/2: transform index
+  int g;      // kinds 1/2: tile index within the pass
+  int need;   // kind 2: column tiles of this transform to wait for
+};
+
+struct ManyTransform {
+  long long off;     // element offset of the transform in the packed data
+  long long ws_off;  // element offset of its workspace
+  int lgN, lg1, lg2, c1, c2;
+  int tab;           // index of its two-level W_N table
+};
+
+struct ManyArgs {
+  const float2* in;
+  float2* out;
+  float2* ws;
+  const ManyItem* items;
+  const ManyTransform* trs;
+  const long long* offs;
+  const float2* stage_tw;      // stage tables, lengths 2^1..2^12 back to back
+  const int* stage_tw_off;     // [13] offset of the table for length 2^lg
+  const float2* ft_tab;        // two-level tables per four-step length
+  const int* ft_off;           // [17] offset of (lo, hi) for lgN; lo then hi
+  int* head;
+  int* done;
+  int* status;
+  int nitems;
+  int conj;
+  int inv;
+  long long wait_budget;
+};
+
+struct ManyPlan {
+  void* d_mem = nullptr;   // items, transforms, offsets, tables, counters
+  size_t counters_bytes = 0;
+  int* d_counters = nullptr;
+  ManyArgs args{};
+  int nitems = 0;
+  int grid = 0;
+  long long total = 0;
+};
+
+constexpr int kManyThreads = 256;
+
+// the four-step split used for 2^13..2^16 inside the persistent kernel
+__host__ __device__ constexpr int many_lg1(int lgN) { return lgN <= 14 ? 7 : 8; }
+__host__ __device__ constexpr int many_lg2(int lgN) { return lgN - many_lg1(lgN); }
+
+template <int LG, int C, bool ICF, bool OCF>
+constexpr int many_smem() { return TileCfg<LG, C, ICF, OCF>::SMEM_BYTES; }
+
+template <int LG>
+constexpr int many_batch_smem() {
+  if constexpr (LG == 0) {
+    return 0;
+  } else {
+    return cmax(TileCfg<LG, (LG >= 4) ? (4096 >> LG) : 256, false, false>::SMEM_BYTES, many_batch_smem<LG - 1>());
+  }
+}
+
+// dynamic shared memory: the largest tile any item kind needs
+constexpr int kManySmem = cmax(many_batch_smem<12>(),
+                               cmax(cmax(many_smem<7, 32, true, true>(), many_smem<8, 16, true, true>()),
+                                    cmax(cmax(many_smem<6, 64, false, true>(), many_smem<7, 32, false, true>()),
+                                         many_smem<8, 16, false, true>())));
+
+__device__ __forceinline__ bool many_wait(const int* flag, int target, long long budget) {
+  const long long t0 = clock64();
+  while (true) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+    if (v >= target) return true;
+    if (clock64() - t0 > budget) return false;
+    __nanosleep(64);
+  }
+}
+
+template <int LG>
+__device__ __forceinline__ void many_batch_tile(const ManyArgs& m, const ManyItem& it, TileArgs& a, float2* smem,
+                                                long long* s_off) {
+  constexpr int C = (LG >= 4) ? (4096 >> LG) : 256;
+  for (int c = threadIdx.x; c < C; c += kManyThreads) s_off[c] = c < it.ncols ? m.offs[it.tr + c] : 0;
+  __syncthreads();
+  a.in = m.in;
+  a.out = m.out;
+  a.tw = m.stage_tw + m.stage_tw_off[LG];
+  a.tiles_per_batch = 1LL << 40;
+  a.in_sn = a.out_sn = 1;
+  a.ncols = it.ncols;
+  a.col_off = s_off;
+  const float sc = m.inv ? 1.0f / (float)(1 << LG) : 1.0f;
+  a.scale_out = (m.conj || m.inv) ? 1 : 0;
+  a.sx = sc;
+  a.sy = m.conj ? -sc : sc;
+  tile_body<LG, C, false, false, true>(a, 0, smem);
+}
+
+template <int LG1>
+__device__ __forceinline__ void many_col_tile(const ManyArgs& m, const ManyItem& it, const ManyTransform& t,
+                                              TileArgs& a, float2* smem) {
+  constexpr int C = 4096 >> LG1;
+  const long long N2 = 1LL << t.lg2;
+  a.in = m.in + t.off;
+  a.out = m.ws + t.ws_off;
+  a.tw = m.stage_tw + m.stage_tw_off[LG1];
+  a.tiles_per_batch = 1LL << 40;
+  a.in_gstride = a.out_gstride = C;
+  a.in_sc = a.out_sc = 1;
+  a.in_sn = a.out_sn = N2;
+  a.ncols = N2;
+  a.ft_lo = m.ft_tab + m.ft_off[t.lgN];
+  a.ft_hi = a.ft_lo + (1 << ((t.lgN + 1) / 2));
+  a.ft_lgN = t.lgN;
+  a.ft_s = (t.lgN + 1) / 2;
+  a.stream_out = 0;
+  tile_body<LG1, C, true, true>(a, it.g, smem);
+}
+
+template <int LG2>
+__device__ __forceinline__ void many_row_tile(const ManyArgs& m, const ManyItem& it, const ManyTransform& t,
+                                              TileArgs& a, float2* smem) {
+  constexpr int C = 4096 >> LG2;
+  const long long N1 = 1LL << t.lg1, N2 = 1LL << LG2;
+  a.in = m.ws + t.ws_off;
+  a.out = m.out + t.off;
+  a.tw = m.stage_tw + m.stage_tw_off[LG2];
+  a.tiles_per_batch = 1LL << 40;
+  a.in_gstride = C * N2;
+  a.in_sc = N2;
+  a.in_sn = 1;
+  a.out_gstride = C;
+  a.out_sc = 1;
+  a.out_sn = N1;
+  a.ncols = N1;
+  a.stream_in = 0;
+  const float sc = m.inv ? 1.0f / (float)(1LL << t.lgN) : 1.0f;
+  a.scale_out = (m.conj || m.inv) ? 1 : 0;
+  a.sx = sc;
+  a.sy = m.conj ? -sc : sc;
+  tile_body<LG2, C, false, true>(a, it.g, smem);
+}
+
+__global__ void __launch_bounds__(kManyThreads, 3) many_kernel(const ManyArgs m) {
+  extern __shared__ float2 smem[];
+  __shared__ int s_item;
+  __shared__ long long s_off[256];
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(m.head, 1);
+    __syncthreads();
+    const int idx = s_item;
+    if (idx >= m.nitems) return;
+    const ManyItem it = m.items[idx];
+    TileArgs a;
+    memset(&a, 0, sizeof(a));
+    a.stream_in = 1;
+    a.stream_out = 1;
+    if (it.kind == 0) {
+      a.conj_in = m.conj;
+      switch (it.lg) {
+        case 1: many_batch_tile<1>(m, it, a, smem, s_off); break;
+        case 2: many_batch_tile<2>(m, it, a, smem, s_off); break;
+        case 3: many_batch_tile<3>(m, it, a, smem, s_off); break;
+        case 4: many_batch_tile<4>(m, it, a, smem, s_off); break;
+        case 5: many_batch_tile<5>(m, it, a, smem, s_off); break;
+        case 6: many_batch_tile<6>(m, it, a, smem, s_off); break;
+        case 7: many_batch_tile<7>(m, it, a, smem, s_off); break;
+        case 8: many_batch_tile<8>(m, it, a, smem, s_off); break;
+        case 9: many_batch_tile<9>(m, it, a, smem, s_off); break;
+        case 10: many_batch_tile<10>(m, it, a, smem, s_off); break;
+        case 11: many_batch_tile<11>(m, it, a, smem, s_off); break;
+        case 12: many_batch_tile<12>(m, it, a, smem, s_off); break;
+      }
+    } else if (it.kind == 1) {
+      const ManyTransform t = m.trs[it.tr];
+      a.conj_in = m.conj;
+      if (t.lg1 == 7) many_col_tile<7>(m, it, t, a, smem);
+      else many_col_tile<8>(m, it, t, a, smem);
+      // publish: every thread's stores are visible before the counter moves
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(m.done + it.tr, 1);
+    } else {
+      const ManyTransform t = m.trs[it.tr];
+      if (threadIdx.x == 0) {
+        if (!many_wait(m.done + it.tr, it.need, m.wait_budget)) atomicExch(m.status, FFT_ERR_TIMEOUT);
+      }
+      __syncthreads();
+      if (t.lg2 == 6) many_row_tile<6>(m, it, t, a, smem);
+      else if (t.lg2 == 7) many_row_tile<7>(m, it, t, a, smem);
+      else many_row_tile<8>(m, it, t, a, smem);
+    }
+    __syncthreads();  // smem and s_item are reused by the next item
+  }
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
+  if (count > (1 << 24)) return FFT_ERR_INVALID_ARG;
+  std::vector<int> lg(count);
+  long long total = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const int64_t n = lengths[i];
+    if (n < 2 || n > (1 << 16) || (n & (n - 1))) return FFT_ERR_INVALID_ARG;
+    int l = 0;
+    while ((1LL << l) < n) ++l;
+    lg[i] = l;
+    total += n;
+  }
+  std::vector<long long> off(count);
+  {
+    long long o = 0;
+    for (int64_t i = 0; i < count; ++i) {
+      off[i] = o;
+      o += lengths[i];
+    }
+  }
+  // batch tiles: group transforms of equal length (<= 2^12), largest first
+  std::vector<ManyItem> col_items, batch_items, row_items;
+  std::vector<long long> slots;
+  std::vector<ManyTransform> trs;
+  long long ws_total = 0;
+  for (int L = 12; L >= 1; --L) {
+    const int C = (L >= 4) ? (4096 >> L) : 256;
+    std::vector<long long> grp;
+    for (int64_t i = 0; i < count; ++i)
+      if (lg[i] == L) grp.push_back(off[i]);
+    for (size_t s = 0; s < grp.size(); s += C) {
+      ManyItem it{};
+      it.kind = 0;
+      it.lg = L;
+      it.ncols = (int)std::min<size_t>(C, grp.size() - s);
+      it.tr = (int)slots.size();
+      for (int c = 0; c < it.ncols; ++c) slots.push_back(grp[s + c]);
+      batch_items.push_back(it);
+    }
+  }
+  // four-step transforms, largest first
+  for (int L = 16; L >= 13; --L) {
+    for (int64_t i = 0; i < count; ++i) {
+      if (lg[i] != L) continue;
+      ManyTransform t{};
+      t.off = off[i];
+      t.ws_off = ws_total;
+      t.lgN = L;
+      t.lg1 = many_lg1(L);
+      t.lg2 = many_lg2(L);
+      t.c1 = 4096 >> t.lg1;
+      t.c2 = 4096 >> t.lg2;
+      ws_total += 1LL << L;
+      const int tr = (int)trs.size();
+      const int ncol_tiles = (int)((1LL << t.lg2) / t.c1);
+      const int nrow_tiles = (int)((1LL << t.lg1) / t.c2);
+      for (int g = 0; g < ncol_tiles; ++g) col_items.push_back(ManyItem{1, t.lg1, t.c1, tr, g, 0});
+      for (int g = 0; g < nrow_tiles; ++g) row_items.push_back(ManyItem{2, t.lg2, t.c2, tr, g, ncol_tiles});
+      trs.push_back(t);
+    }
+  }
+  std::vector<ManyItem> items;
+  items.insert(items.end(), col_items.begin(), col_items.end());
+  items.insert(items.end(), batch_items.begin(), batch_items.end());
+  items.insert(items.end(), row_items.begin(), row_items.end());
+  if (getenv("GBFFT_TEST_MISSING_PRODUCER") && atoi(getenv("GBFFT_TEST_MISSING_PRODUCER")) && !row_items.empty()) {
+    // test hook: one row tile waits for a column tile that does not exist
+    for (ManyItem& it : items)
+      if (it.kind == 2) {
+        it.need += 1;
+        break;
+      }
+  }
+
+  // twiddle tables: stage tables for every tile length 1..12, two-level W_N
+  // tables for every four-step length 13..16
+  int stage_off[13] = {0};
+  int st_total = 0;
+  for (int L = 1; L <= 12; ++L) {
+    stage_off[L] = st_total;
+    st_total += stage_tw_size(L) + 1;
+  }
+  int ft_off[17] = {0};
+  int ft_total = 0;
+  for (int L = 13; L <= 16; ++L) {
+    ft_off[L] = ft_total;
+    ft_total += (1 << ((L + 1) / 2)) + (1 << (L - (L + 1) / 2));
+  }
+
+  ManyPlan* mp = new (std::nothrow) ManyPlan;
+  if (!mp) return FFT_ERR_ALLOC;
+  p->many = mp;
+  const size_t b_items = al256(sizeof(ManyItem) * (items.size() + 1));
+  const size_t b_trs = al256(sizeof(ManyTransform) * (trs.size() + 1));
+  const size_t b_slots = al256(sizeof(long long) * (slots.size() + 1));
+  const size_t b_st = al256(sizeof(float2) * (st_total + 1));
+  const size_t b_sto = al256(sizeof(int) * 13);
+  const size_t b_ft = al256(sizeof(float2) * (ft_total + 1));
+  const size_t b_fto = al256(sizeof(int) * 17);
+  const size_t b_cnt = al256(sizeof(int) * (trs.size() + 2));
+  const size_t total_b = b_items + b_trs + b_slots + b_st + b_sto + b_ft + b_fto + b_cnt;
+  char* base = nullptr;
+  if (cudaMalloc(&base, total_b) != cudaSuccess) return FFT_ERR_ALLOC;
+  mp->d_mem = base;
+  char* q = base;
+  ManyItem* d_items = (ManyItem*)q; q += b_items;
+  ManyTransform* d_trs = (ManyTransform*)q; q += b_trs;
+  long long* d_slots = (long long*)q; q += b_slots;
+  float2* d_st = (float2*)q; q += b_st;
+  int* d_sto = (int*)q; q += b_sto;
+  float2* d_ft = (float2*)q; q += b_ft;
+  int* d_fto = (int*)q; q += b_fto;
+  int* d_cnt = (int*)q;
+  if (cudaMemcpy(d_items, items.data(), sizeof(ManyItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (trs.size() && cudaMemcpy(d_trs, trs.data(), sizeof(ManyTransform) * trs.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (slots.size() && cudaMemcpy(d_slots, slots.data(), sizeof(long long) * slots.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(d_sto, stage_off, sizeof(stage_off), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_fto, ft_off, sizeof(ft_off), cudaMemcpyHostToDevice) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  for (int L = 1; L <= 12; ++L)
+    if (launch_gen_stage_twiddles(d_st + stage_off[L], L, 0) != cudaSuccess) return FFT_ERR_CUDA;
+  for (int L = 13; L <= 16; ++L) {
+    const int s = (L + 1) / 2;
+    if (launch_gen_power_twiddles(d_ft + ft_off[L], L, 1LL << s, 1, 0) != cudaSuccess ||
+        launch_gen_power_twiddles(d_ft + ft_off[L] + (1 << s), L, 1LL << (L - s), 1LL << s, 0) != cudaSuccess)
+      return FFT_ERR_CUDA;
+  }
+  // status word: reuse the plan's convention (a separate small allocation)
+  if (cudaMalloc(&p->d_tables, 256) != cudaSuccess) return FFT_ERR_ALLOC;
+  p->d_status = (int*)p->d_tables;
+  if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return FFT_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FFT_ERR_CUDA;
+
+  if (cudaFuncSetAttribute(many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kManySmem) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, many_kernel, kManyThreads, kManySmem) != cudaSuccess ||
+      per_sm < 1)
+    return FFT_ERR_CUDA;
+  mp->grid = (int)std::min<long long>((long long)per_sm * sms, (long long)items.size());
+  mp->nitems = (int)items.size();
+  mp->total = total;
+  mp->d_counters = d_cnt;
+  mp->counters_bytes = sizeof(int) * (trs.size() + 2);
+
+  ManyArgs& m = mp->args;
+  m.items = d_items;
+  m.trs = d_trs;
+  m.offs = d_slots;
+  m.stage_tw = d_st;
+  m.stage_tw_off = d_sto;
+  m.ft_tab = d_ft;
+  m.ft_off = d_fto;
+  m.head = d_cnt;
+  m.done = d_cnt + 1;
+  m.status = p->d_status;
+  m.nitems = mp->nitems;
+  const bool starve = getenv("GBFFT_TEST_MISSING_PRODUCER") && atoi(getenv("GBFFT_TEST_MISSING_PRODUCER"));
+  m.wait_budget = starve ? 2000000LL : 4000000000LL;  // ~1 ms for the test hook, ~2 s otherwise
+
+  p->n = total;
+  p->ws_bytes = (size_t)ws_total * 8;
+  p->launches = 1;
+  return FFT_OK;
+}
+
+void many_plan_free(fft_plan* p) {
+  if (!p->many) return;
+  if (p->many->d_mem) cudaFree(p->many->d_mem);
+  delete p->many;
+  p->many = nullptr;
+}
+
+int many_exec(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
+  ManyPlan* mp = p->many;
+  if (!mp) return FFT_ERR_INVALID_ARG;
+  if (p->ws_bytes && !p->ws) return FFT_ERR_NO_WORKSPACE;
+  ManyArgs m = mp->args;
+  m.in = in;
+  m.out = out;
+  m.ws = (float2*)p->ws;
+  const int inv = dir & FFT_INVERSE, adj = (dir & FFT_ADJOINT) ? 1 : 0;
+  m.conj = inv ^ adj;
+  m.inv = inv;
+  if (cudaMemsetAsync(mp->d_counters, 0, mp->counters_bytes, s) != cudaSuccess) return FFT_ERR_CUDA;
+  void* args[] = {(void*)&m};
+  if (cudaLaunchKernel((const void*)many_kernel, dim3(mp->grid), dim3(kManyThreads), args, kManySmem, s) !=
+      cudaSuccess)
+    return FFT_ERR_CUDA;
+  return FFT_OK;
+}
+
 }  // namespace gbfft

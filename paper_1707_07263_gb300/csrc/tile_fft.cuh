@@ -120,6 +120,9 @@ struct TileArgs {
   float sx, sy;
   int stream_in;    // 1: read with evict-first (.cs) hint; 0: keep in L2 (.cg)
   int stream_out;   // 1: write with evict-first (.cs) hint
+  // Per-column element offsets (OFFS variants only): column c of the tile
+  // starts at in + col_off[c] / out + col_off[c]; in_sc/out_sc are unused.
+  const long long* col_off;
 };
 
 template <int R>
@@ -145,7 +148,7 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
   }
 }
 
-template <int LG, int C, bool IN_CF, bool OUT_CF, int S>
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false>
 __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                            const TileArgs& a, const float2* gin, float2* gout,
                                            long long col0, const float2* epi_tab) {
@@ -177,7 +180,7 @@ __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const bool ok = (col0 + cc[i]) < a.ncols;
-      const float2* p = gin + cc[i] * a.in_sc + (long long)jj[i] * a.in_sn;
+      const float2* p = (OFFS ? gin + (ok ? a.col_off[cc[i]] : 0) : gin + cc[i] * a.in_sc) + (long long)jj[i] * a.in_sn;
       const long long step = (long long)LR * a.in_sn;
       if (a.stream_in) {
 #pragma unroll
@@ -231,7 +234,7 @@ __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT
       for (int q = 0; q < R; ++q) v[q] = make_float2(v[q].x * a.sx, v[q].y * a.sy);
     }
     if (ok) {
-      float2* p = gout + c * a.out_sc + (long long)j * a.out_sn;
+      float2* p = (OFFS ? gout + a.col_off[c] : gout + c * a.out_sc) + (long long)j * a.out_sn;
       const long long step = (long long)NS * a.out_sn;
       if (a.stream_out) {
 #pragma unroll
@@ -251,19 +254,19 @@ __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT
       for (int q = 0; q < R; ++q) sm[cc[i] * LP + pidx(base + q * NS)] = v[i * R + q];
     }
     __syncthreads();
-    tile_stage<LG, C, IN_CF, OUT_CF, S + 1>(v, sm, a, gin, gout, col0, epi_tab);
+    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS>(v, sm, a, gin, gout, col0, epi_tab);
   }
 }
 
-template <int LG, int C, bool IN_CF, bool OUT_CF>
-__global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
-    tile_fft_kernel(const TileArgs a) {
+// One tile of a pass: tile index `tile` of the launch described by `a`, using
+// `smem` (TileCfg::SMEM_BYTES).  Shared by the one-tile-per-CTA kernel below
+// and the persistent uneven-batch kernel.
+template <int LG, int C, bool IN_CF, bool OUT_CF, bool OFFS = false>
+__device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, float2* smem) {
   using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
-  extern __shared__ float2 smem[];
   float2* sm = smem;
   float2* epi_tab = smem + Cfg::SM_TILE;
 
-  const long long tile = (long long)blockIdx.x;
   const long long b = tile / a.tiles_per_batch;
   const long long g = tile - b * a.tiles_per_batch;
   const long long col0 = g * C;
@@ -284,7 +287,14 @@ __global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
   }
 
   float2 v[Cfg::P];
-  tile_stage<LG, C, IN_CF, OUT_CF, 0>(v, sm, a, gin, gout, col0, epi_tab);
+  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS>(v, sm, a, gin, gout, col0, epi_tab);
+}
+
+template <int LG, int C, bool IN_CF, bool OUT_CF>
+__global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
+    tile_fft_kernel(const TileArgs a) {
+  extern __shared__ float2 smem[];
+  tile_body<LG, C, IN_CF, OUT_CF>(a, (long long)blockIdx.x, smem);
 }
 
 }  // namespace gbfft

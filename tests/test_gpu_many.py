@@ -1,0 +1,131 @@
+"""Uneven-length batches in one persistent launch (fft_plan_create_many):
+parity against the oracle per transform, CUDA-graph capture and replay, and
+the bounded inter-CTA wait turning a missing producer into FFT_ERR_TIMEOUT."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1707_07263_gb300 import _lib, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load()
+
+
+class ManyPlan:
+    def __init__(self, lib, lengths, d=0):
+        arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
+        h = lib.fft_plan_create_many(arr, len(lengths), d, 0)
+        assert h, _lib.ERRORS.get(lib.fft_last_error())
+        self.lib, self.h = lib, ctypes.c_void_p(h)
+        ws = lib.fft_plan_workspace_bytes(self.h)
+        self.ws = torch.empty(max(ws, 256), dtype=torch.uint8, device="cuda")
+        if ws:
+            assert lib.fft_plan_set_workspace(self.h, ctypes.c_void_p(self.ws.data_ptr())) == 0
+
+    def run(self, x, d, out=None, stream=None):
+        out = torch.empty_like(x) if out is None else out
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        rc = self.lib.fft_exec_dir(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), d,
+                                   ctypes.c_void_p(s))
+        assert rc == 0, _lib.ERRORS.get(rc, rc)
+        return out
+
+    def status(self):
+        return self.lib.fft_status(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def __del__(self):
+        self.lib.fft_destroy(self.h)
+
+
+def oracle_many(x, lengths, d):
+    outs, o = [], 0
+    for n in lengths:
+        seg = x[o:o + n].astype(np.complex128)
+        if d == 3:
+            outs.append(oracle.transform(seg, oracle.FORWARD) / n)
+        else:
+            outs.append(oracle.transform(seg, d))
+        o += n
+    return outs
+
+
+def check(got, refs, lengths, what):
+    o = 0
+    for n, ref in zip(lengths, refs):
+        err = oracle.rel_l2(got[o:o + n], ref)
+        assert err <= 5e-7 * max(1, np.log2(n)), f"{what}: length {n} at {o}: {err:.3e}"
+        o += n
+
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_many_every_length(lib, d):
+    # every supported length, twice, in a shuffled order
+    lengths = [1 << e for e in list(range(1, 17)) * 2]
+    rng = np.random.Generator(np.random.PCG64(5))
+    rng.shuffle(lengths)
+    x = workloads.packed_cgauss(lengths, seed=300 + d)
+    p = ManyPlan(lib, lengths, d)
+    got = p.run(torch.from_numpy(x).cuda(), d).cpu().numpy()
+    check(got, oracle_many(x, lengths, d), lengths, f"dir {d}")
+    assert p.status() == 0
+
+
+def test_many_config5_shape(lib):
+    """Lengths drawn like the uneven-batch workload (exponent uniform over
+    8..16), 256 transforms, every transform checked."""
+    lengths = workloads.uneven_lengths(256, seed=workloads.seed_for(4)).tolist()
+    x = workloads.packed_cgauss(lengths, seed=workloads.seed_for(4, 2))
+    p = ManyPlan(lib, lengths, 0)
+    got = p.run(torch.from_numpy(x).cuda(), 0).cpu().numpy()
+    check(got, oracle_many(x, lengths, 0), lengths, "cfg5-shaped")
+
+
+def test_many_in_place_and_graph_replay(lib):
+    lengths = workloads.uneven_lengths(64, seed=17).tolist()
+    p = ManyPlan(lib, lengths, 0)
+    x1 = workloads.packed_cgauss(lengths, seed=18)
+    x2 = workloads.packed_cgauss(lengths, seed=19)
+    buf = torch.from_numpy(x1).cuda()
+    out = torch.empty_like(buf)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p.run(buf, 0, out, stream=s)      # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        p.run(buf, 0, out, stream=s)
+    for x in (x1, x2):
+        buf.copy_(torch.from_numpy(x))
+        g.replay()
+        torch.cuda.synchronize()
+        check(out.cpu().numpy(), oracle_many(x, lengths, 0), lengths, "graph replay")
+    # in place
+    buf.copy_(torch.from_numpy(x2))
+    p.run(buf, 0, buf)
+    torch.cuda.synchronize()
+    check(buf.cpu().numpy(), oracle_many(x2, lengths, 0), lengths, "in place")
+
+
+def test_many_bounded_wait_reports_timeout(lib, monkeypatch):
+    """A row tile told to wait for a column tile that never comes gives up
+    after its budget and reports FFT_ERR_TIMEOUT instead of hanging."""
+    monkeypatch.setenv("GBFFT_TEST_MISSING_PRODUCER", "1")
+    lengths = [1 << 14, 1 << 10, 1 << 16]
+    p = ManyPlan(lib, lengths, 0)
+    x = torch.from_numpy(workloads.packed_cgauss(lengths, seed=3)).cuda()
+    p.run(x, 0)
+    torch.cuda.synchronize()
+    assert p.status() == -5
+    monkeypatch.delenv("GBFFT_TEST_MISSING_PRODUCER")
+    p2 = ManyPlan(lib, lengths, 0)     # a fresh plan is unaffected
+    p2.run(x, 0)
+    assert p2.status() == 0
