@@ -464,13 +464,152 @@ def run_case(args):
     lib.fft_destroy(h)
 
 
+# ------------------------------------------------------------------------------------
+# measurement-only workloads (not the contract line): tc, large, many
+# ------------------------------------------------------------------------------------
+def _time_fn(torch, fn, iters, warmup, stream):
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(iters):
+            fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / iters
+
+
+def run_measure(args):
+    import torch
+    import oracle
+    from paper_1707_07263_gb300 import _lib, api, workloads
+    lib = _lib.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    peak, _ = measured_peaks()
+    res = []
+
+    def plan(n, batch, prec):
+        h = lib.fft_plan_create(n, batch, 0, prec)
+        if not h:
+            return None, None
+        h = ctypes.c_void_p(h)
+        ws = lib.fft_plan_workspace_bytes(h)
+        wsb = torch.empty(max(ws, 1), dtype=torch.uint8, device=dev)
+        if ws:
+            _lib.check(lib.fft_plan_set_workspace(h, ctypes.c_void_p(wsb.data_ptr())))
+        return h, wsb
+
+    def run_plan(h, x, y, d=0):
+        _lib.check(lib.fft_exec_dir(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), d, sh))
+
+    if args.workload == "tc":
+        precs = [("fp32", 0), ("tc_bf16", 1), ("tc_fp16", 2), ("tc_bf16_split", 3), ("tc_fp16_split", 4)]
+        for lg in (12, 16, 20):
+            n = 1 << lg
+            batch = TOTAL // n
+            xh = workloads.cgauss(n, batch, seed=workloads.seed_for(3) + lg)
+            x = torch.from_numpy(xh.reshape(-1)).to(dev)
+            y = torch.empty_like(x)
+            rows = 2
+            ref = oracle.fft(xh[:rows].astype(np.complex128))
+            for name, pc in precs:
+                h, wsb = plan(n, batch, pc)
+                if h is None:
+                    res.append({"n": n, "prec": name, "unsupported": True})
+                    continue
+                ms = _time_fn(torch, lambda: run_plan(h, x, y), args.steps, args.warmup, stream)
+                got = y[: rows * n].cpu().numpy().reshape(rows, n)
+                err = float(oracle.rel_l2_rows(got, ref).max())
+                nl = lib.fft_plan_launches(h)
+                res.append({"n": n, "batch": batch, "prec": name, "us": round(ms * 1e3, 1),
+                            "gflops": round(flops(n, batch) / (ms * 1e-3) / 1e9, 1),
+                            "hbm_gbs_per_launch": round(16.0 * n * batch * nl / (ms * 1e-3) / 1e9, 1),
+                            "hbm_frac_per_launch": round(16.0 * n * batch * nl / (ms * 1e-3) / 1e9 / peak, 4),
+                            "launches": nl, "rel_l2_max": float(f"{err:.3e}")})
+                lib.fft_destroy(h)
+        desc = "precision variants: batched N in {2^12, 2^16, 2^20}, batch 2^26/N, CN(0,1); FP32 vs TC radix-16"
+    elif args.workload == "large":
+        x = torch.from_numpy(workloads.uniform(1 << 26, 1, workloads.seed_for(2)).reshape(-1)).to(dev)
+        y = torch.empty_like(x)
+        for lg in (20, 22, 24, 26):
+            n = 1 << lg
+            batch = TOTAL // n
+            h, wsb = plan(n, batch, 0)
+            ms = _time_fn(torch, lambda: run_plan(h, x, y), args.steps, args.warmup, stream)
+            buf = ctypes.create_string_buffer(512)
+            lib.fft_plan_describe(h, buf, 512)
+            res.append({"n": n, "batch": batch, "us": round(ms * 1e3, 1),
+                        "gflops": round(flops(n, batch) / (ms * 1e-3) / 1e9, 1),
+                        "hbm_frac_algorithmic": round(16.0 * n * batch / (ms * 1e-3) / 1e9 / peak, 4),
+                        "plan": buf.value.decode()})
+            lib.fft_destroy(h)
+        img = torch.from_numpy(workloads.sar_image(8192, 8192, seed=workloads.seed_for(2, 1)).reshape(-1)).to(dev)
+        h2 = ctypes.c_void_p(lib.fft_plan_create_2d(8192, 8192, 1, 0, 0))
+        ms = _time_fn(torch, lambda: run_plan(h2, img, y), args.steps, args.warmup, stream)
+        res.append({"n": "8192x8192", "us": round(ms * 1e3, 1),
+                    "gflops": round(flops(1 << 26, 1) / (ms * 1e-3) / 1e9, 1),
+                    "hbm_frac_algorithmic": round(16.0 * (1 << 26) / (ms * 1e-3) / 1e9 / peak, 4), "launches": 2})
+        lib.fft_destroy(h2)
+        desc = "large transforms: four-step 1-D N = 2^20..2^26 (2^26 points per launch), 2-D 8192x8192 SAR image"
+    elif args.workload == "many":
+        lengths = workloads.uneven_lengths(4096, seed=workloads.seed_for(4)).tolist()
+        total = int(sum(lengths))
+        xh = workloads.packed_cgauss(lengths, seed=workloads.seed_for(4, 2))
+        wh = workloads.real_weights(total, seed=workloads.seed_for(4, 1))
+        x = torch.from_numpy(xh).to(dev)
+        w2 = torch.from_numpy(2.0 * wh.astype(np.float32) ** 2).to(dev)
+        p = api.get_plan("many", (total,), len(lengths), "fp32", dev, lengths=tuple(lengths))
+        X = torch.empty_like(x)
+        G = torch.empty_like(x)
+        gx = torch.empty_like(x)
+
+        def step():
+            p.exec_ptr(x.data_ptr(), X.data_ptr(), 0, stream)          # forward, one persistent launch
+            torch.mul(X, w2, out=G)                                     # dL/dX* = 2 w^2 X
+            p.exec_ptr(G.data_ptr(), gx.data_ptr(), 2, stream)          # backward: adjoint F^H
+
+        with torch.cuda.stream(stream):
+            step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            step()
+        ms = _time_fn(torch, g.replay, args.steps, args.warmup, stream)
+        ms_fwd = _time_fn(torch, lambda: p.exec_ptr(x.data_ptr(), X.data_ptr(), 0, stream), args.steps,
+                          args.warmup, stream)
+        fl = sum(flops(n, 1) for n in lengths)
+        # gradient check on a sample of transforms against the oracle
+        gxh = gx.cpu().numpy()
+        offs = np.concatenate([[0], np.cumsum(lengths)])
+        errs = []
+        for i in range(0, len(lengths), 97):
+            a, b = offs[i], offs[i + 1]
+            ref = oracle.spectral_loss_grad(xh[a:b].astype(np.complex128), wh[a:b].astype(np.float64))
+            errs.append(oracle.rel_l2(gxh[a:b], ref))
+        res.append({"transforms": len(lengths), "points": total, "graph_step_us": round(ms * 1e3, 1),
+                    "forward_us": round(ms_fwd * 1e3, 1),
+                    "gflops_fwd_plus_bwd": round(2 * fl / (ms * 1e-3) / 1e9, 1),
+                    "gflops_fwd": round(fl / (ms_fwd * 1e-3) / 1e9, 1),
+                    "hbm_frac_fwd": round(16.0 * total / (ms_fwd * 1e-3) / 1e9 / peak, 4),
+                    "grad_rel_l2_max_sampled": float(f"{max(errs):.3e}"), "grad_samples": len(errs)})
+        desc = ("uneven batch: 4096 transforms, lengths 2^e with e uniform over 8..16, CN(0,1); "
+                "graph-captured forward + loss gradient + adjoint backward")
+    print(json.dumps({"workload": args.workload, "desc": desc, "results": res,
+                      "peak_hbm_gbs": peak}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -483,6 +622,8 @@ def main():
         args.warmup = 3
     if args.case:
         run_case(args)
+    elif args.workload != "cfg2" and args.impl != "reference":
+        run_measure(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -45,7 +45,11 @@ struct fft_plan {
   int ft_s;
 
   // tensor-core radix-16 path (prec != FFT_PREC_FP32)
-  void* d_tc;   // DFT matrices (hi/lo splits) in BF16/FP16
+  void* d_tc;   // full twiddle tables of the tensor-core passes
+  const gbfft::TileKernelInfo* ktc1;
+  const gbfft::TileKernelInfo* ktc2;
+  const float2* tctw1;
+  const float2* tctw2;
 
   size_t ws_bytes;
   void* ws;

@@ -1,0 +1,28 @@
+// tc_inst_fp16s.cu -- tensor-core tile-FFT variants, precision code 4 (fp16s).
+#include "tc_fft.cuh"
+#include "tile_registry.h"
+
+namespace gbfft {
+
+#define GBFFT_TC(LG, C, ICF, OCF, MAP, PREC) \
+  {(const void*)&tc_fft_kernel<LG, C, ICF, OCF, PREC>, TileCfg<LG, C, ICF, OCF>::T, \
+   TileCfg<LG, C, ICF, OCF>::SMEM_BYTES, LG, C, MAP}
+
+const TileKernelInfo* tc_kernel_fp16s(int map, int lg, int C) {
+  static const TileKernelInfo tab[] = {
+      GBFFT_TC(8, jj_cols(8), false, false, MAP_JJ, 4),
+      GBFFT_TC(10, jj_cols(10), false, false, MAP_JJ, 4),
+      GBFFT_TC(12, jj_cols(12), false, false, MAP_JJ, 4),
+      GBFFT_TC(8, 16, true, true, MAP_CC, 4),
+      GBFFT_TC(8, 16, false, true, MAP_JC, 4),
+      GBFFT_TC(10, 8, true, true, MAP_CC, 4),
+      GBFFT_TC(10, 8, false, true, MAP_JC, 4),
+      GBFFT_TC(12, 2, true, true, MAP_CC, 4),
+      GBFFT_TC(12, 2, false, true, MAP_JC, 4),
+  };
+  for (const TileKernelInfo& k : tab)
+    if (k.map == map && k.lg == lg && k.C == C) return &k;
+  return nullptr;
+}
+
+}  // namespace gbfft

@@ -148,10 +148,12 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
   }
 }
 
+// One pass S of the tile: gather, twiddle, R-point DFT, scatter (with the
+// barriers that separate it from its neighbours).
 template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false>
-__device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
-                                           const TileArgs& a, const float2* gin, float2* gout,
-                                           long long col0, const float2* epi_tab) {
+__device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
+                                          const TileArgs& a, const float2* gin, float2* gout,
+                                          long long col0, const float2* epi_tab) {
   using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
   constexpr int L = Cfg::L, P = Cfg::P, T = Cfg::T, NST = Cfg::NST, LP = Cfg::LP;
   constexpr int LGR = radix_lgr(LG, S), R = 1 << LGR;
@@ -254,8 +256,16 @@ __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT
       for (int q = 0; q < R; ++q) sm[cc[i] * LP + pidx(base + q * NS)] = v[i * R + q];
     }
     __syncthreads();
-    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS>(v, sm, a, gin, gout, col0, epi_tab);
   }
+}
+
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false>
+__device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
+                                           const TileArgs& a, const float2* gin, float2* gout,
+                                           long long col0, const float2* epi_tab) {
+  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS>(v, sm, a, gin, gout, col0, epi_tab);
+  if constexpr (S + 1 < TileCfg<LG, C, IN_CF, OUT_CF>::NST)
+    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS>(v, sm, a, gin, gout, col0, epi_tab);
 }
 
 // One tile of a pass: tile index `tile` of the launch described by `a`, using
