@@ -543,17 +543,25 @@ def run_measure(args):
             ms = _time_fn(torch, lambda: run_plan(h, x, y), args.steps, args.warmup, stream)
             buf = ctypes.create_string_buffer(512)
             lib.fft_plan_describe(h, buf, 512)
+            nl = lib.fft_plan_launches(h)
             res.append({"n": n, "batch": batch, "us": round(ms * 1e3, 1),
                         "gflops": round(flops(n, batch) / (ms * 1e-3) / 1e9, 1),
                         "hbm_frac_algorithmic": round(16.0 * n * batch / (ms * 1e-3) / 1e9 / peak, 4),
+                        "hbm_frac_per_launch": round(16.0 * n * batch * nl / (ms * 1e-3) / 1e9 / peak, 4),
                         "plan": buf.value.decode()})
             lib.fft_destroy(h)
         img = torch.from_numpy(workloads.sar_image(8192, 8192, seed=workloads.seed_for(2, 1)).reshape(-1)).to(dev)
         h2 = ctypes.c_void_p(lib.fft_plan_create_2d(8192, 8192, 1, 0, 0))
+        ws2 = torch.empty(max(1, lib.fft_plan_workspace_bytes(h2)), dtype=torch.uint8, device=dev)
+        if lib.fft_plan_workspace_bytes(h2):
+            _lib.check(lib.fft_plan_set_workspace(h2, ctypes.c_void_p(ws2.data_ptr())))
         ms = _time_fn(torch, lambda: run_plan(h2, img, y), args.steps, args.warmup, stream)
+        nl2 = lib.fft_plan_launches(h2)
         res.append({"n": "8192x8192", "us": round(ms * 1e3, 1),
                     "gflops": round(flops(1 << 26, 1) / (ms * 1e-3) / 1e9, 1),
-                    "hbm_frac_algorithmic": round(16.0 * (1 << 26) / (ms * 1e-3) / 1e9 / peak, 4), "launches": 2})
+                    "hbm_frac_algorithmic": round(16.0 * (1 << 26) / (ms * 1e-3) / 1e9 / peak, 4),
+                    "hbm_frac_per_launch": round(16.0 * (1 << 26) * nl2 / (ms * 1e-3) / 1e9 / peak, 4),
+                    "launches": nl2})
         lib.fft_destroy(h2)
         desc = "large transforms: four-step 1-D N = 2^20..2^26 (2^26 points per launch), 2-D 8192x8192 SAR image"
     elif args.workload == "many":

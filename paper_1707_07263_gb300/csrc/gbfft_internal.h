@@ -6,11 +6,24 @@
 #include <stdint.h>
 
 #include "../../include/gbfft.h"
+#include "tile_fft.cuh"
 
 namespace gbfft {
 
 struct TileKernelInfo;
 struct ManyPlan;
+
+// One launch of a multi-pass plan.  Buffers are named by role so a plan can
+// run on any (in, out) pair: 0 = the caller's input, 1 = the caller's output,
+// 2 = the workspace.  conj-in is applied by the first pass, the output
+// scale / conj by the last.
+struct PassDesc {
+  const TileKernelInfo* k;
+  TileArgs a;
+  int in_role, out_role;
+  long long ntiles;
+};
+constexpr int kMaxPasses = 4;
 
 enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3 };
 
@@ -59,4 +72,13 @@ struct fft_plan {
 
   gbfft::ManyPlan* many;
   int launches;
+
+  // multi-pass plans (four-step with two or three passes, 2-D)
+  gbfft::PassDesc pass[gbfft::kMaxPasses];
+  int npass;
+  int lg3;            // three-pass split: log2 N3
+  const float2* tw3;  // stage table of the third length
+  const float2* ft2_lo;  // two-level table of the second four-step level
+  const float2* ft2_hi;
+  int ft2_s;
 };

@@ -15,6 +15,7 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -86,42 +87,65 @@ static int default_cols(int lg) {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Allocates and fills the plan's twiddle tables: stage tables for up to two
-// lengths and, for four-step plans, the two-level W_N table.
-static int build_tables(fft_plan* p, int lgA, int lgB, int lgN) {
-  const size_t szA = lgA > 0 ? (size_t)stage_tw_size(lgA) : 0;
-  const size_t szB = lgB > 0 ? (size_t)stage_tw_size(lgB) : 0;
-  size_t lo = 0, hi = 0;
-  if (lgN > 0) {
-    p->ft_s = (lgN + 1) / 2;
-    lo = (size_t)1 << p->ft_s;
-    hi = (size_t)1 << (lgN - p->ft_s);
+// Allocates and fills the plan's twiddle tables in one device buffer: stage
+// tables for up to three lengths (lgs[i] > 0) and two-level W_N tables for up
+// to two four-step levels (lgNs[i] > 0).  Also the device status word.
+static int build_tables_multi(fft_plan* p, const int lgs[3], const int lgNs[2]) {
+  size_t off = 0, stage_off[3], lo_off[2], hi_off[2];
+  size_t lo_n[2] = {0, 0}, hi_n[2] = {0, 0};
+  int ss[2] = {0, 0};
+  for (int i = 0; i < 3; ++i) {
+    stage_off[i] = off;
+    off += align256((lgs[i] > 0 ? (size_t)stage_tw_size(lgs[i]) : 0) * 8 + 8);
   }
-  const size_t offA = 0;
-  const size_t offB = offA + align256(szA * 8 + 8);
-  const size_t offLo = offB + align256(szB * 8 + 8);
-  const size_t offHi = offLo + align256(lo * 8 + 8);
-  const size_t offSt = offHi + align256(hi * 8 + 8);
-  const size_t total = offSt + 256;
+  for (int i = 0; i < 2; ++i) {
+    if (lgNs[i] > 0) {
+      ss[i] = (lgNs[i] + 1) / 2;
+      lo_n[i] = (size_t)1 << ss[i];
+      hi_n[i] = (size_t)1 << (lgNs[i] - ss[i]);
+    }
+    lo_off[i] = off;
+    off += align256(lo_n[i] * 8 + 8);
+    hi_off[i] = off;
+    off += align256(hi_n[i] * 8 + 8);
+  }
+  const size_t st_off = off;
+  off += 256;
   char* base = nullptr;
-  if (cudaMalloc(&base, total) != cudaSuccess) return FFT_ERR_ALLOC;
+  if (cudaMalloc(&base, off) != cudaSuccess) return FFT_ERR_ALLOC;
   p->d_tables = base;
-  p->tw1 = (const float2*)(base + offA);
-  p->tw2 = (const float2*)(base + offB);
-  p->ft_lo = (const float2*)(base + offLo);
-  p->ft_hi = (const float2*)(base + offHi);
-  p->d_status = (int*)(base + offSt);
+  p->tw1 = (const float2*)(base + stage_off[0]);
+  p->tw2 = (const float2*)(base + stage_off[1]);
+  p->tw3 = (const float2*)(base + stage_off[2]);
+  p->ft_lo = (const float2*)(base + lo_off[0]);
+  p->ft_hi = (const float2*)(base + hi_off[0]);
+  p->ft_s = ss[0];
+  p->ft2_lo = (const float2*)(base + lo_off[1]);
+  p->ft2_hi = (const float2*)(base + hi_off[1]);
+  p->ft2_s = ss[1];
+  p->d_status = (int*)(base + st_off);
   cudaStream_t s = 0;
   if (cudaMemsetAsync(p->d_status, 0, sizeof(int), s) != cudaSuccess) return FFT_ERR_CUDA;
-  if (lgA > 0 && launch_gen_stage_twiddles((float2*)p->tw1, lgA, s) != cudaSuccess) return FFT_ERR_CUDA;
-  if (lgB > 0 && launch_gen_stage_twiddles((float2*)p->tw2, lgB, s) != cudaSuccess) return FFT_ERR_CUDA;
-  if (lgN > 0) {
-    if (launch_gen_power_twiddles((float2*)p->ft_lo, lgN, (long long)lo, 1, s) != cudaSuccess) return FFT_ERR_CUDA;
-    if (launch_gen_power_twiddles((float2*)p->ft_hi, lgN, (long long)hi, (long long)lo, s) != cudaSuccess)
+  const float2* st[3] = {p->tw1, p->tw2, p->tw3};
+  for (int i = 0; i < 3; ++i)
+    if (lgs[i] > 0 && launch_gen_stage_twiddles((float2*)st[i], lgs[i], s) != cudaSuccess) return FFT_ERR_CUDA;
+  const float2* los[2] = {p->ft_lo, p->ft2_lo};
+  const float2* his[2] = {p->ft_hi, p->ft2_hi};
+  for (int i = 0; i < 2; ++i) {
+    if (lgNs[i] <= 0) continue;
+    if (launch_gen_power_twiddles((float2*)los[i], lgNs[i], (long long)lo_n[i], 1, s) != cudaSuccess ||
+        launch_gen_power_twiddles((float2*)his[i], lgNs[i], (long long)hi_n[i], (long long)lo_n[i], s) !=
+            cudaSuccess)
       return FFT_ERR_CUDA;
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return FFT_ERR_CUDA;
   return FFT_OK;
+}
+
+static int build_tables(fft_plan* p, int lgA, int lgB, int lgN) {
+  const int lgs[3] = {lgA, lgB, 0};
+  const int lgNs[2] = {lgN, 0};
+  return build_tables_multi(p, lgs, lgNs);
 }
 
 static fft_plan* new_plan() {
@@ -218,85 +242,22 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
   return launch_tile(p->k1, a, a.tiles_per_batch, s);
 }
 
-// ---- four-step: column pass + twiddle, then row pass ------------------------
-static int exec_fourstep(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
-  if (!p->ws) return FFT_ERR_NO_WORKSPACE;
+// ---- multi-pass plans: run the pass list ------------------------------------
+static int exec_passes(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
   const DirXf x = dir_xf(dir, p->n);
-  const long long N = p->n, N1 = 1LL << p->lg1, N2 = 1LL << p->lg2;
-  float2* ws = (float2*)p->ws;
-  // pass 1: tile g = columns [g*C1, g*C1+C1) of the N1 x N2 view x[N2*n1 + n2]
-  TileArgs a;
-  base_args(a);
-  a.in = in;
-  a.out = ws;
-  a.tw = p->tw1;
-  a.tiles_per_batch = N2 / p->c1;
-  a.in_bstride = a.out_bstride = N;
-  a.in_gstride = a.out_gstride = p->c1;
-  a.in_sc = a.out_sc = 1;
-  a.in_sn = a.out_sn = N2;
-  a.ncols = N2;
-  a.ft_lo = p->ft_lo;
-  a.ft_hi = p->ft_hi;
-  a.ft_lgN = p->lg1 + p->lg2;
-  a.ft_s = p->ft_s;
-  a.conj_in = x.conj;
-  a.stream_out = 0;  // the workspace is read back by pass 2: keep it in L2
-  int rc = launch_tile(p->k1, a, a.tiles_per_batch * p->batch, s);
-  if (rc) return rc;
-  // pass 2: tile g = rows k1 in [g*C2, g*C2+C2) of Y, written to X[k1 + N1*k2]
-  TileArgs b;
-  base_args(b);
-  b.in = ws;
-  b.out = out;
-  b.tw = p->tw2;
-  b.tiles_per_batch = N1 / p->c2;
-  b.in_bstride = b.out_bstride = N;
-  b.in_gstride = (long long)p->c2 * N2;
-  b.in_sc = N2;
-  b.in_sn = 1;
-  b.out_gstride = p->c2;
-  b.out_sc = 1;
-  b.out_sn = N1;
-  b.ncols = N1;
-  b.stream_in = 0;
-  set_out_xf(b, x);
-  return launch_tile(p->k2, b, b.tiles_per_batch * p->batch, s);
-}
-
-// ---- 2-D: rows, then columns in place --------------------------------------
-static int exec_2d(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
-  const DirXf x = dir_xf(dir, p->ny * p->nx);
-  const long long ny = p->ny, nx = p->nx;
-  TileArgs a;
-  base_args(a);
-  const int C = p->k1->C;
-  a.in = in;
-  a.out = out;
-  a.tw = p->tw2;
-  a.tiles_per_batch = (ny * p->batch + C - 1) / C;
-  a.in_gstride = a.out_gstride = (long long)C * nx;
-  a.in_sc = a.out_sc = nx;
-  a.in_sn = a.out_sn = 1;
-  a.ncols = ny * p->batch;
-  a.conj_in = x.conj;
-  a.stream_out = 0;  // read back by the column pass
-  int rc = launch_tile(p->k1, a, a.tiles_per_batch, s);
-  if (rc) return rc;
-  TileArgs b;
-  base_args(b);
-  b.in = out;
-  b.out = out;
-  b.tw = p->tw1;
-  b.tiles_per_batch = nx / p->c2;
-  b.in_bstride = b.out_bstride = ny * nx;
-  b.in_gstride = b.out_gstride = p->c2;
-  b.in_sc = b.out_sc = 1;
-  b.in_sn = b.out_sn = nx;
-  b.ncols = nx;
-  b.stream_in = 0;
-  set_out_xf(b, x);
-  return launch_tile(p->k2, b, b.tiles_per_batch * p->batch, s);
+  float2* roles[3] = {(float2*)in, out, (float2*)p->ws};
+  for (int i = 0; i < p->npass; ++i) {
+    const PassDesc& d = p->pass[i];
+    if ((d.in_role == 2 || d.out_role == 2) && !p->ws) return FFT_ERR_NO_WORKSPACE;
+    TileArgs a = d.a;
+    a.in = roles[d.in_role];
+    a.out = roles[d.out_role];
+    if (i == 0) a.conj_in = x.conj;
+    if (i == p->npass - 1) set_out_xf(a, x);
+    const int rc = launch_tile(d.k, a, d.ntiles, s);
+    if (rc) return rc;
+  }
+  return FFT_OK;
 }
 
 int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
@@ -310,8 +271,8 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
   } else {
     switch (p->kind) {
       case KIND_SINGLE: rc = exec_single(p, fin, fout, dir, s); break;
-      case KIND_FOURSTEP: rc = exec_fourstep(p, fin, fout, dir, s); break;
-      case KIND_2D: rc = exec_2d(p, fin, fout, dir, s); break;
+      case KIND_FOURSTEP:
+      case KIND_2D: rc = exec_passes(p, fin, fout, dir, s); break;
       case KIND_MANY: rc = many_exec(p, fin, fout, dir, s); break;
       default: rc = FFT_ERR_INVALID_ARG;
     }
@@ -351,26 +312,287 @@ static int plan_1d(fft_plan* p, int lgN) {
     return build_tables(p, lgN, 0, 0);
   }
   p->kind = KIND_FOURSTEP;
-  int lg2 = (lgN + 1) / 2;
-  const int force_lg1 = env_int("GBFFT_FORCE_SPLIT", 0);
-  if (force_lg1 > 0 && force_lg1 < lgN && lgN - force_lg1 <= 14 && force_lg1 <= 14) lg2 = lgN - force_lg1;
-  const int lg1 = lgN - lg2;
-  if (lg1 > 14 || lg2 > 14) return FFT_ERR_UNSUPPORTED;
-  p->lg1 = lg1;
-  p->lg2 = lg2;
-  p->c1 = env_int("GBFFT_FORCE_C1", default_cols(lg1));
-  p->c2 = env_int("GBFFT_FORCE_C2", default_cols(lg2));
-  if (p->c1 > (1 << lg2)) p->c1 = 1 << lg2;
-  if (p->c2 > (1 << lg1)) p->c2 = 1 << lg1;
-  p->k1 = tile_kernel(MAP_CC, lg1, p->c1);
-  p->k2 = tile_kernel(MAP_JC, lg2, p->c2);
-  if (!p->k1 || !p->k2) return FFT_ERR_UNSUPPORTED;
-  p->launches = 2;
-  p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
-  int rc = prepare_kernel(p->k1);
-  if (!rc) rc = prepare_kernel(p->k2);
+  int npass = (lgN >= 23) ? 3 : 2;
+  const int force_np = env_int("GBFFT_PASSES", 0);
+  if (force_np == 2 || force_np == 3) npass = force_np;
+  if (p->prec != FFT_PREC_FP32) npass = 2;  // tensor-core kernels are compiled for two-pass splits
+  if (npass == 2 && lgN > 28) return FFT_ERR_UNSUPPORTED;
+  if (npass == 2) {
+    int lg2 = (lgN + 1) / 2;
+    const int force_lg1 = env_int("GBFFT_FORCE_SPLIT", 0);
+    if (force_lg1 > 0 && force_lg1 < lgN && lgN - force_lg1 <= 14 && force_lg1 <= 14) lg2 = lgN - force_lg1;
+    const int lg1 = lgN - lg2;
+    if (lg1 > 14 || lg2 > 14) return FFT_ERR_UNSUPPORTED;
+    p->lg1 = lg1;
+    p->lg2 = lg2;
+    p->c1 = env_int("GBFFT_FORCE_C1", default_cols(lg1));
+    p->c2 = env_int("GBFFT_FORCE_C2", default_cols(lg2));
+    if (p->c1 > (1 << lg2)) p->c1 = 1 << lg2;
+    if (p->c2 > (1 << lg1)) p->c2 = 1 << lg1;
+    p->k1 = tile_kernel(MAP_CC, lg1, p->c1);
+    p->k2 = tile_kernel(MAP_JC, lg2, p->c2);
+    if (!p->k1 || !p->k2) return FFT_ERR_UNSUPPORTED;
+    int rc = prepare_kernel(p->k1);
+    if (!rc) rc = prepare_kernel(p->k2);
+    if (!rc) rc = build_tables(p, lg1, lg2, lgN);
+    if (rc) return rc;
+    const long long N = p->n, N1 = 1LL << lg1, N2 = 1LL << lg2;
+    // pass 1: tile g = columns [g*C1, g*C1+C1) of the N1 x N2 view x[N2*n1 + n2],
+    // scaled by W_N^{n2*k1}, written to the workspace as Y[k1][n2]
+    PassDesc& A = p->pass[0];
+    A.k = p->k1;
+    base_args(A.a);
+    A.a.tw = p->tw1;
+    A.a.tiles_per_batch = N2 / p->c1;
+    A.a.in_bstride = A.a.out_bstride = N;
+    A.a.in_gstride = A.a.out_gstride = p->c1;
+    A.a.in_sc = A.a.out_sc = 1;
+    A.a.in_sn = A.a.out_sn = N2;
+    A.a.ncols = N2;
+    A.a.ft_lo = p->ft_lo;
+    A.a.ft_hi = p->ft_hi;
+    A.a.ft_lgN = lgN;
+    A.a.ft_s = p->ft_s;
+    A.a.stream_out = 0;  // read back by pass 2: keep it in L2
+    A.in_role = 0;
+    A.out_role = 2;
+    A.ntiles = A.a.tiles_per_batch * p->batch;
+    // pass 2: tile g = rows k1 in [g*C2, g*C2+C2) of Y, written to X[k1 + N1*k2]
+    PassDesc& B = p->pass[1];
+    B.k = p->k2;
+    base_args(B.a);
+    B.a.tw = p->tw2;
+    B.a.tiles_per_batch = N1 / p->c2;
+    B.a.in_bstride = B.a.out_bstride = N;
+    B.a.in_gstride = (long long)p->c2 * N2;
+    B.a.in_sc = N2;
+    B.a.in_sn = 1;
+    B.a.out_gstride = p->c2;
+    B.a.out_sc = 1;
+    B.a.out_sn = N1;
+    B.a.ncols = N1;
+    B.a.stream_in = 0;
+    B.in_role = 2;
+    B.out_role = 1;
+    B.ntiles = B.a.tiles_per_batch * p->batch;
+    p->npass = 2;
+    p->launches = 2;
+    p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
+    return FFT_OK;
+  }
+  // three passes, N = N1 * N2 * N3 (M = N2 * N3):
+  //   A  columns of length N1 over stride M, scaled by W_N^{m*k1}     in -> ws
+  //   B  per k1, columns of length N2 over stride N3 of the M-point
+  //      row, scaled by W_M^{n3*k2}                                   ws -> ws (in place)
+  //   C  rows of length N3, written to X[k1 + N1*k2 + N1*N2*k3]      ws -> out
+  const int l1 = (lgN + 2) / 3, l2 = (lgN - l1 + 1) / 2, l3 = lgN - l1 - l2;
+  if (l1 > 14 || l2 > 14 || l3 > 14 || l3 < 1) return FFT_ERR_UNSUPPORTED;
+  p->lg1 = l1;
+  p->lg2 = l2;
+  p->lg3 = l3;
+  const long long N = p->n, N1 = 1LL << l1, N2 = 1LL << l2, N3 = 1LL << l3, M = N2 * N3;
+  const int cA = (int)std::min<long long>(default_cols(l1), M);
+  const int cB = (int)std::min<long long>(default_cols(l2), N3);
+  const int cC = (int)std::min<long long>(default_cols(l3), N1);
+  const TileKernelInfo* kA = tile_kernel(MAP_CC, l1, cA);
+  const TileKernelInfo* kB = tile_kernel(MAP_CC, l2, cB);
+  const TileKernelInfo* kC = tile_kernel(MAP_JC, l3, cC);
+  if (!kA || !kB || !kC) return FFT_ERR_UNSUPPORTED;
+  int rc = prepare_kernel(kA);
+  if (!rc) rc = prepare_kernel(kB);
+  if (!rc) rc = prepare_kernel(kC);
+  const int lgs[3] = {l1, l2, l3};
+  const int lgNs[2] = {lgN, l2 + l3};
+  if (!rc) rc = build_tables_multi(p, lgs, lgNs);
   if (rc) return rc;
-  return build_tables(p, lg1, lg2, lgN);
+  p->k1 = kA;
+  p->k2 = kC;
+  p->c1 = cA;
+  p->c2 = cC;
+  PassDesc& A = p->pass[0];
+  A.k = kA;
+  base_args(A.a);
+  A.a.tw = p->tw1;
+  A.a.tiles_per_batch = M / cA;
+  A.a.in_bstride = A.a.out_bstride = N;
+  A.a.in_gstride = A.a.out_gstride = cA;
+  A.a.in_sc = A.a.out_sc = 1;
+  A.a.in_sn = A.a.out_sn = M;
+  A.a.ncols = M;
+  A.a.ft_lo = p->ft_lo;
+  A.a.ft_hi = p->ft_hi;
+  A.a.ft_lgN = lgN;
+  A.a.ft_s = p->ft_s;
+  A.a.stream_out = 0;
+  A.in_role = 0;
+  A.out_role = 2;
+  A.ntiles = A.a.tiles_per_batch * p->batch;
+  PassDesc& B = p->pass[1];
+  B.k = kB;
+  base_args(B.a);
+  B.a.tw = p->tw2;
+  B.a.tiles_per_batch = N3 / cB;
+  B.a.in_bstride = B.a.out_bstride = M;  // batch index = (b, k1): row (b*N1 + k1) of length M
+  B.a.in_gstride = B.a.out_gstride = cB;
+  B.a.in_sc = B.a.out_sc = 1;
+  B.a.in_sn = B.a.out_sn = N3;
+  B.a.ncols = N3;
+  B.a.ft_lo = p->ft2_lo;
+  B.a.ft_hi = p->ft2_hi;
+  B.a.ft_lgN = l2 + l3;
+  B.a.ft_s = p->ft2_s;
+  B.a.stream_in = 0;
+  B.a.stream_out = 0;
+  B.in_role = 2;
+  B.out_role = 2;
+  B.ntiles = B.a.tiles_per_batch * p->batch * N1;
+  PassDesc& Cp = p->pass[2];
+  Cp.k = kC;
+  base_args(Cp.a);
+  Cp.a.tw = p->tw3;
+  Cp.a.tiles_per_batch = N1 / cC;  // tile = ((b, k2), k1 group)
+  Cp.a.nb1 = N2;
+  Cp.a.in_b2stride = Cp.a.out_b2stride = N;
+  Cp.a.in_bstride = N3;
+  Cp.a.out_bstride = N1;
+  Cp.a.in_gstride = cC * M;
+  Cp.a.out_gstride = cC;
+  Cp.a.in_sc = M;
+  Cp.a.in_sn = 1;
+  Cp.a.out_sc = 1;
+  Cp.a.out_sn = N1 * N2;
+  Cp.a.ncols = N1;
+  Cp.a.stream_in = 0;
+  Cp.in_role = 2;
+  Cp.out_role = 1;
+  Cp.ntiles = Cp.a.tiles_per_batch * N2 * p->batch;
+  p->npass = 3;
+  p->launches = 3;
+  p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
+  return FFT_OK;
+}
+
+// 2-D plan (Sec. 2.3.2: rows, then columns).  Rows: one on-chip pass over all
+// ny*batch rows.  Columns: for ny <= 2^10 one column pass of C >= 8 adjacent
+// columns (>= 64 contiguous bytes per row); taller images split the column
+// length ny = Y1*Y2 into two column passes (the four-step split applied along
+// y), so every column tile stays 16 columns wide.
+static int build_2d(fft_plan* p, int ly, int lx) {
+  const long long ny = p->ny, nx = p->nx, img = ny * nx;
+  const TileKernelInfo* kr = tile_kernel(MAP_JJ, lx, jj_cols(lx));
+  if (!kr) return FFT_ERR_UNSUPPORTED;
+  int rc = prepare_kernel(kr);
+  if (rc) return rc;
+  const int two = (ly >= 11 && !env_int("GBFFT_2D_ONE_COLUMN_PASS", 0)) ? 1 : 0;
+  PassDesc& R = p->pass[0];
+  R.k = kr;
+  base_args(R.a);
+  const int Cr = kr->C;
+  R.a.tiles_per_batch = (ny * p->batch + Cr - 1) / Cr;
+  R.a.in_gstride = R.a.out_gstride = (long long)Cr * nx;
+  R.a.in_sc = R.a.out_sc = nx;
+  R.a.in_sn = R.a.out_sn = 1;
+  R.a.ncols = ny * p->batch;
+  R.a.stream_out = 0;  // read back by the column pass
+  R.in_role = 0;
+  R.out_role = two ? 2 : 1;
+  R.ntiles = R.a.tiles_per_batch;
+  p->k1 = kr;
+  p->c1 = Cr;
+  if (!two) {
+    const int C = (int)std::min<long long>(env_int("GBFFT_FORCE_C2", default_cols(ly)), nx);
+    const TileKernelInfo* kc = tile_kernel(MAP_CC, ly, C);
+    if (!kc) return FFT_ERR_UNSUPPORTED;
+    rc = prepare_kernel(kc);
+    const int lgs[3] = {ly, lx, 0};
+    const int lgNs[2] = {0, 0};
+    if (!rc) rc = build_tables_multi(p, lgs, lgNs);
+    if (rc) return rc;
+    R.a.tw = p->tw2;
+    PassDesc& Cp = p->pass[1];
+    Cp.k = kc;
+    base_args(Cp.a);
+    Cp.a.tw = p->tw1;
+    Cp.a.tiles_per_batch = nx / C;
+    Cp.a.in_bstride = Cp.a.out_bstride = img;
+    Cp.a.in_gstride = Cp.a.out_gstride = C;
+    Cp.a.in_sc = Cp.a.out_sc = 1;
+    Cp.a.in_sn = Cp.a.out_sn = nx;
+    Cp.a.ncols = nx;
+    Cp.a.stream_in = 0;
+    Cp.in_role = 1;
+    Cp.out_role = 1;
+    Cp.ntiles = Cp.a.tiles_per_batch * p->batch;
+    p->k2 = kc;
+    p->c2 = C;
+    p->npass = 2;
+    p->launches = 2;
+    p->ws_bytes = 0;
+    return FFT_OK;
+  }
+  const int ly1 = ly / 2, ly2 = ly - ly1;
+  const long long Y1 = 1LL << ly1, Y2 = 1LL << ly2;
+  const int ca = (int)std::min<long long>(default_cols(ly1), nx);
+  const int cb = (int)std::min<long long>(default_cols(ly2), nx);
+  const TileKernelInfo* ka = tile_kernel(MAP_CC, ly1, ca);
+  const TileKernelInfo* kb = tile_kernel(MAP_CC, ly2, cb);
+  if (!ka || !kb) return FFT_ERR_UNSUPPORTED;
+  rc = prepare_kernel(ka);
+  if (!rc) rc = prepare_kernel(kb);
+  const int lgs[3] = {ly1, lx, ly2};
+  const int lgNs[2] = {ly, 0};
+  if (!rc) rc = build_tables_multi(p, lgs, lgNs);
+  if (rc) return rc;
+  R.a.tw = p->tw2;
+  // column pass A: y = y1*Y2 + y2; per (image, y2) the FFT over y1 of C
+  // adjacent columns, scaled by W_ny^{y2*ky1}; in place in the workspace
+  PassDesc& A = p->pass[1];
+  A.k = ka;
+  base_args(A.a);
+  A.a.tw = p->tw1;
+  A.a.tiles_per_batch = nx / ca;
+  A.a.nb1 = Y2;
+  A.a.in_b2stride = A.a.out_b2stride = img;
+  A.a.in_bstride = A.a.out_bstride = nx;
+  A.a.in_gstride = A.a.out_gstride = ca;
+  A.a.in_sc = A.a.out_sc = 1;
+  A.a.in_sn = A.a.out_sn = Y2 * nx;
+  A.a.ncols = nx;
+  A.a.ft_lo = p->ft_lo;
+  A.a.ft_hi = p->ft_hi;
+  A.a.ft_lgN = ly;
+  A.a.ft_s = p->ft_s;
+  A.a.ft_by_batch = 1;
+  A.a.stream_in = 0;
+  A.a.stream_out = 0;
+  A.in_role = 2;
+  A.out_role = 2;
+  A.ntiles = A.a.tiles_per_batch * Y2 * p->batch;
+  // column pass B: per (image, ky1) the FFT over y2, written to row ky1 + Y1*ky2
+  PassDesc& B = p->pass[2];
+  B.k = kb;
+  base_args(B.a);
+  B.a.tw = p->tw3;
+  B.a.tiles_per_batch = nx / cb;
+  B.a.nb1 = Y1;
+  B.a.in_b2stride = B.a.out_b2stride = img;
+  B.a.in_bstride = Y2 * nx;
+  B.a.out_bstride = nx;
+  B.a.in_gstride = B.a.out_gstride = cb;
+  B.a.in_sc = B.a.out_sc = 1;
+  B.a.in_sn = nx;
+  B.a.out_sn = Y1 * nx;
+  B.a.ncols = nx;
+  B.a.stream_in = 0;
+  B.in_role = 2;
+  B.out_role = 1;
+  B.ntiles = B.a.tiles_per_batch * Y1 * p->batch;
+  p->k2 = kb;
+  p->c2 = cb;
+  p->npass = 3;
+  p->launches = 3;
+  p->ws_bytes = (size_t)img * (size_t)p->batch * 8;
+  return FFT_OK;
 }
 
 }  // namespace gbfft
@@ -434,16 +656,7 @@ fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int
   p->prec = prec;
   p->lg1 = ly;
   p->lg2 = lx;
-  p->k1 = tile_kernel(MAP_JJ, lx, jj_cols(lx));
-  p->c1 = p->k1 ? p->k1->C : 0;
-  p->c2 = env_int("GBFFT_FORCE_C2", default_cols(ly));
-  if (p->c2 > nx) p->c2 = (int)nx;
-  p->k2 = tile_kernel(MAP_CC, ly, p->c2);
-  p->launches = 2;
-  int rc = (p->k1 && p->k2) ? FFT_OK : FFT_ERR_UNSUPPORTED;
-  if (!rc) rc = prepare_kernel(p->k1);
-  if (!rc) rc = prepare_kernel(p->k2);
-  if (!rc) rc = build_tables(p, ly, lx, 0);
+  int rc = build_2d(p, ly, lx);
   if (rc != FFT_OK) {
     free_plan(p);
     set_err(rc);

@@ -246,7 +246,7 @@ __device__ __forceinline__ void tc_stage(float2* sm, const TileArgs& a, const fl
     tc_pass<LG, C, IN_CF, OUT_CF, S, PREC>(sm, a, gin, gout, col0, A);
   } else {
     float2 v[Cfg::P];
-    tile_pass<LG, C, IN_CF, OUT_CF, S>(v, sm, a, gin, gout, col0, epi_tab);
+    tile_pass<LG, C, IN_CF, OUT_CF, S>(v, sm, a, gin, gout, col0, 0, epi_tab);
   }
   if constexpr (S + 1 < Cfg::NST) tc_stage<LG, C, IN_CF, OUT_CF, S + 1, PREC>(sm, a, gin, gout, col0, epi_tab, A);
 }

@@ -123,6 +123,13 @@ struct TileArgs {
   // Per-column element offsets (OFFS variants only): column c of the tile
   // starts at in + col_off[c] / out + col_off[c]; in_sc/out_sc are unused.
   const long long* col_off;
+  // Optional outer batch: the batch index bq = tile / tiles_per_batch splits
+  // into b2 = bq / nb1 and b = bq % nb1, adding b2*in_b2stride (out_b2stride).
+  // nb1 = 0 means no outer batch.
+  long long nb1, in_b2stride, out_b2stride;
+  // Four-step twiddle multiplier: 0 = the column index g*C + c, 1 = the
+  // (inner) batch index b.
+  int ft_by_batch;
 };
 
 template <int R>
@@ -153,7 +160,7 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false>
 __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                           const TileArgs& a, const float2* gin, float2* gout,
-                                          long long col0, const float2* epi_tab) {
+                                          long long col0, long long bidx, const float2* epi_tab) {
   using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
   constexpr int L = Cfg::L, P = Cfg::P, T = Cfg::T, NST = Cfg::NST, LP = Cfg::LP;
   constexpr int LGR = radix_lgr(LG, S), R = 1 << LGR;
@@ -224,7 +231,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       // four-step twiddle W_N^{n2*k}, n2 = col0 + c, k = j + q*NS
       //   = W_N^{n2*j} * W_N^{n2*NS*q}; the second factor is the per-column
       //   table epi_tab[c*16 + q] built at kernel start.
-      const unsigned n2 = (unsigned)(col0 + c);
+      const unsigned n2 = a.ft_by_batch ? (unsigned)bidx : (unsigned)(col0 + c);
       const unsigned m = n2 * (unsigned)j;
       const unsigned mask = (1u << a.ft_s) - 1u;
       const float2 base = cmul(__ldg(a.ft_lo + (m & mask)), __ldg(a.ft_hi + (m >> a.ft_s)));
@@ -262,10 +269,10 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
 template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false>
 __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                            const TileArgs& a, const float2* gin, float2* gout,
-                                           long long col0, const float2* epi_tab) {
-  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS>(v, sm, a, gin, gout, col0, epi_tab);
+                                           long long col0, long long bidx, const float2* epi_tab) {
+  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS>(v, sm, a, gin, gout, col0, bidx, epi_tab);
   if constexpr (S + 1 < TileCfg<LG, C, IN_CF, OUT_CF>::NST)
-    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS>(v, sm, a, gin, gout, col0, epi_tab);
+    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS>(v, sm, a, gin, gout, col0, bidx, epi_tab);
 }
 
 // One tile of a pass: tile index `tile` of the launch described by `a`, using
@@ -277,18 +284,24 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, flo
   float2* sm = smem;
   float2* epi_tab = smem + Cfg::SM_TILE;
 
-  const long long b = tile / a.tiles_per_batch;
+  long long b = tile / a.tiles_per_batch;
   const long long g = tile - b * a.tiles_per_batch;
+  long long b2 = 0;
+  if (a.nb1) {
+    b2 = b / a.nb1;
+    b -= b2 * a.nb1;
+  }
   const long long col0 = g * C;
-  const float2* gin = a.in + b * a.in_bstride + g * a.in_gstride;
-  float2* gout = a.out + b * a.out_bstride + g * a.out_gstride;
+  const float2* gin = a.in + b2 * a.in_b2stride + b * a.in_bstride + g * a.in_gstride;
+  float2* gout = a.out + b2 * a.out_b2stride + b * a.out_bstride + g * a.out_gstride;
 
   if (Cfg::EPI && a.ft_lgN) {
     // per-column step factors W_N^{n2*NS_last*q}, q = 0..15
     constexpr int NS_LAST = 1 << radix_lgns(LG, Cfg::NST - 1);
     for (int e = threadIdx.x; e < C * 16; e += Cfg::T) {
       const int c = e >> 4, q = e & 15;
-      const unsigned m = (unsigned)(col0 + c) * (unsigned)NS_LAST * (unsigned)q;
+      const unsigned n2 = a.ft_by_batch ? (unsigned)b : (unsigned)(col0 + c);
+      const unsigned m = n2 * (unsigned)NS_LAST * (unsigned)q;
       const unsigned mm = m & ((1u << a.ft_lgN) - 1u);
       const unsigned mask = (1u << a.ft_s) - 1u;
       epi_tab[e] = cmul(__ldg(a.ft_lo + (mm & mask)), __ldg(a.ft_hi + (mm >> a.ft_s)));
@@ -297,7 +310,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, flo
   }
 
   float2 v[Cfg::P];
-  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS>(v, sm, a, gin, gout, col0, epi_tab);
+  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS>(v, sm, a, gin, gout, col0, b, epi_tab);
 }
 
 template <int LG, int C, bool IN_CF, bool OUT_CF>

@@ -182,6 +182,26 @@ def test_fourstep_other_splits(lib, monkeypatch, split):
     assert_rows(got, oracle_dir(x, 0), tol32(n), f"split 2^{split} x 2^{20 - split}")
 
 
+@pytest.mark.parametrize("lg,batch", [(15, 2), (18, 2), (21, 1), (23, 1)])
+@pytest.mark.parametrize("d", ["fwd", "inv"])
+def test_three_pass_split(lib, monkeypatch, lg, batch, d):
+    """N = N1*N2*N3 in three passes (the default from 2^23 up), forced at
+    smaller sizes too."""
+    monkeypatch.setenv("GBFFT_PASSES", "3")
+    n = 1 << lg
+    x = workloads.cgauss(n, batch, seed=5500 + lg)
+    got = run_1d(lib, x, DIRS[d])
+    assert_rows(got, oracle_dir(x, DIRS[d]), tol32(n), f"three-pass {d} N=2^{lg}")
+
+
+def test_two_pass_forced_at_2_24(lib, monkeypatch):
+    monkeypatch.setenv("GBFFT_PASSES", "2")
+    n = 1 << 24
+    x = workloads.uniform(n, 1, seed=5600)
+    got = run_1d(lib, x, 0)
+    assert_rows(got, oracle.fft(x.astype(np.complex128)), tol32(n), "two-pass 2^24")
+
+
 # --- full-size large transforms (config 3a) ----------------------------------------
 @pytest.mark.parametrize("lg", [24, 26])
 def test_fourstep_full_size(lib, lg):
@@ -203,7 +223,8 @@ def run_2d(lib, x: np.ndarray, d: int) -> np.ndarray:
 
 
 @pytest.mark.parametrize("ny,nx,batch", [(2, 2, 1), (8, 32, 2), (64, 16, 1), (256, 512, 1), (32, 4096, 1),
-                                         (4096, 64, 1), (1024, 1024, 1)])
+                                         (4096, 64, 1), (1024, 1024, 1), (2048, 16, 3), (16384, 8, 1),
+                                         (8192, 2, 2)])
 @pytest.mark.parametrize("d", ["fwd", "inv"])
 def test_2d(lib, ny, nx, batch, d):
     x = workloads.cgauss(ny * nx, batch, seed=ny * 31 + nx).reshape(batch, ny, nx)
@@ -212,6 +233,15 @@ def test_2d(lib, ny, nx, batch, d):
     tol = tol32(ny * nx)
     for b in range(batch):
         assert oracle.rel_l2(got[b], ref[b]) <= tol, f"2-D {ny}x{nx} {d}"
+
+
+def test_2d_one_column_pass_forced(lib, monkeypatch):
+    monkeypatch.setenv("GBFFT_2D_ONE_COLUMN_PASS", "1")
+    x = workloads.cgauss(4096 * 32, 2, seed=77).reshape(2, 4096, 32)
+    got = run_2d(lib, x, 0)
+    ref = oracle.fft2(x.astype(np.complex128))
+    for b in range(2):
+        assert oracle.rel_l2(got[b], ref[b]) <= tol32(4096 * 32)
 
 
 def test_2d_sar_full_size(lib):
