@@ -170,6 +170,12 @@ def workload_large():
     return "1D complex64 FFT via the four-step split, N = 2^24 and 2^26, batch 1, U[-1,1]", items
 
 
+def _describe(lib, h) -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib.fft_plan_describe(h, buf, 512)
+    return buf.value.decode()
+
+
 def flops(n, batch):
     return 5.0 * n * np.log2(n) * batch
 
@@ -224,10 +230,19 @@ def run_gpu(args):
 
     # one plan per (n, batch); inputs resident in HBM before timing
     plans, bufs = {}, {}
+    tuned = {}
     for label, n, batch, d in items:
         key = (n, batch)
         if key not in plans:
-            h = lib.fft_plan_create(n, batch, 0, 0)
+            if args.tuned:
+                # autotuner (native search, cached per GPU model); untimed set-up
+                from paper_1707_07263_gb300 import tune
+                cfg = tune.tuned_config(n, batch, 0, dev)
+                tuned[f"2^{int(np.log2(n))}"] = cfg
+                c = _lib.FftPlanConfig.from_dict(cfg)
+                h = lib.fft_plan_create_config(n, batch, 0, 0, ctypes.byref(c))
+            else:
+                h = lib.fft_plan_create(n, batch, 0, 0)
             if not h:
                 raise RuntimeError(f"plan {n}x{batch}: {_lib.ERRORS.get(lib.fft_last_error())}")
             h = ctypes.c_void_p(h)
@@ -325,7 +340,7 @@ def run_gpu(args):
                     m = nn * bb
                     dx[:m].copy_(host_in[:m], non_blocking=True)
                     h2d += m * 8
-                    p = api.get_plan("1d", (nn,), bb, "fp32", dev)
+                    p = api.get_plan("1d", (nn,), bb, "fp32", dev, tuned=args.tuned)
                     p.exec_ptr(dx.data_ptr(), dy.data_ptr(), dd, stream)
                     host_out[:m].copy_(dy[:m], non_blocking=True)
                     d2h += m * 8
@@ -381,6 +396,8 @@ def run_gpu(args):
         "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": int(launches_per_step * K),
+        "plans": {f"2^{int(np.log2(n))}": _describe(lib, plans[(n, b)][0]) for _, n, b, _ in items},
+        "autotuned": tuned if args.tuned else None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -622,6 +639,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--case", type=int, default=0, help="run one plan of 2^CASE points (profiling case)")
+    ap.add_argument("--tuned", type=int, default=1, help="1: plans from the autotuner (default), 0: planner defaults")
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--dir", type=int, default=0)
     ap.add_argument("--prec", type=int, default=0)

@@ -101,6 +101,36 @@ GBFFT_API int fft_exec(fft_plan* plan, const void* in, void* out, void* stream);
  * tables serve every direction); used for the adjoint in backpropagation. */
 GBFFT_API int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* stream);
 
+/* Explicit plan configuration (all fields <= 0 mean "planner default";
+ * tma < 0 means default).  npass: 1 = one on-chip pass (n <= 2^14), 2 = two
+ * passes N = 2^lg1 * 2^(lgN-lg1), 3 = three passes 2^lg1 * 2^lg2 * 2^lg3.
+ * c1, c2, c3: adjacent transforms (columns) per CTA of each pass, 1..16.
+ * tma: single pass only, 1 = persistent TMA-staged kernel, 0 = register path.
+ * These are the knobs of the autotuner (fft_autotune). */
+typedef struct fft_plan_config {
+  int npass, lg1, lg2, c1, c2, c3, tma;
+} fft_plan_config;
+
+/* As fft_plan_create, with an explicit configuration (NULL = defaults).
+ * Returns NULL with FFT_ERR_UNSUPPORTED if the configuration has no
+ * compiled kernel. */
+GBFFT_API fft_plan* fft_plan_create_config(int64_t n, int64_t batch, int dir, int prec, const fft_plan_config* cfg);
+
+/* The configuration a 1-D plan was built with. */
+GBFFT_API int fft_plan_get_config(const fft_plan* plan, fft_plan_config* out);
+
+/* Autotuner: builds every candidate configuration for (n, batch, prec) --
+ * one or two or three passes, the split lengths near the even split, columns
+ * per CTA around the default, TMA staging on/off -- times each with CUDA
+ * events over `iters` executions (after 3 untimed ones) on the caller's
+ * device buffers in/out (n*batch complex64 each) and workspace ws of ws_bytes
+ * (>= n*batch*8 bytes), and writes the fastest configuration to *best and its
+ * mean time in microseconds to *best_us.  Synchronises `stream`.  The buffers'
+ * contents are overwritten.  Plans are created and destroyed internally, so
+ * call it outside any stream capture.  Only FFT_PREC_FP32 has choices. */
+GBFFT_API int fft_autotune(int64_t n, int64_t batch, int prec, void* in, void* out, void* ws, size_t ws_bytes,
+                           void* stream, int iters, fft_plan_config* best, float* best_us);
+
 /* Frees the plan and everything the library allocated for it.  NULL-safe.
  * The caller must not use the plan afterwards. */
 GBFFT_API void fft_destroy(fft_plan* plan);

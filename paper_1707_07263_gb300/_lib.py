@@ -26,6 +26,22 @@ ERRORS = {
     -7: "FFT_ERR_ALLOC",
 }
 
+class FftPlanConfig(ctypes.Structure):
+    """fft_plan_config of include/gbfft.h."""
+    _fields_ = [(name, ctypes.c_int) for name in ("npass", "lg1", "lg2", "c1", "c2", "c3", "tma")]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "FftPlanConfig":
+        c = cls()
+        c.tma = -1
+        for k, v in d.items():
+            setattr(c, k, int(v))
+        return c
+
+
 # name -> (restype, argtypes); the full exported surface of include/gbfft.h
 _i64, _int, _vp, _sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
 SIGNATURES = {
@@ -44,6 +60,10 @@ SIGNATURES = {
     "fft_plan_describe": (_int, [_vp, ctypes.c_char_p, _sz]),
     "fft_status": (_int, [_vp, _vp]),
     "fft_exec_noalloc": (_int, [_i64, _i64, _int, _vp, _vp, _vp]),
+    "fft_plan_create_config": (_vp, [_i64, _i64, _int, _int, ctypes.POINTER(FftPlanConfig)]),
+    "fft_plan_get_config": (_int, [_vp, ctypes.POINTER(FftPlanConfig)]),
+    "fft_autotune": (_int, [_i64, _i64, _int, _vp, _vp, _vp, _sz, _vp, _int, ctypes.POINTER(FftPlanConfig),
+                            ctypes.POINTER(ctypes.c_float)]),
     "fft_last_error": (_int, []),
     "fft_error_string": (ctypes.c_char_p, [_int]),
 }

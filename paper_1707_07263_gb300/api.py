@@ -45,7 +45,7 @@ class Plan:
     workspace.  ``kind`` is "1d", "2d" or "many"."""
 
     def __init__(self, kind: str, shape, batch: int = 1, dir: int = FORWARD, prec="fp32",
-                 device=None, lengths=None):
+                 device=None, lengths=None, config: dict | None = None):
         self.lib = L.load()
         self.kind = kind
         self.shape = tuple(shape)
@@ -54,7 +54,10 @@ class Plan:
         self.prec = _prec_code(prec)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
-            if kind == "1d":
+            if kind == "1d" and config is not None:
+                cfg = L.FftPlanConfig.from_dict(config)
+                h = self.lib.fft_plan_create_config(int(shape[0]), self.batch, self.dir, self.prec, ctypes.byref(cfg))
+            elif kind == "1d":
                 h = self.lib.fft_plan_create(int(shape[0]), self.batch, self.dir, self.prec)
             elif kind == "2d":
                 h = self.lib.fft_plan_create_2d(int(shape[0]), int(shape[1]), self.batch, self.dir, self.prec)
@@ -120,14 +123,21 @@ _cache: dict = {}
 _cache_lock = threading.Lock()
 
 
-def get_plan(kind: str, shape, batch: int, prec="fp32", device=None, lengths=None) -> Plan:
-    """Cached plan (twiddle tables are built once per shape/precision/device)."""
+def get_plan(kind: str, shape, batch: int, prec="fp32", device=None, lengths=None, tuned: bool = False) -> Plan:
+    """Cached plan (twiddle tables are built once per shape/precision/device).
+    tuned=True builds 1-D plans from the autotuner's cached configuration
+    (tuning the shape first if it has never been tuned on this GPU model)."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    key = (kind, tuple(shape), int(batch), _prec_code(prec), dev.index, tuple(lengths) if lengths is not None else None)
+    key = (kind, tuple(shape), int(batch), _prec_code(prec), dev.index,
+           tuple(lengths) if lengths is not None else None, bool(tuned and kind == "1d"))
     with _cache_lock:
         p = _cache.get(key)
         if p is None:
-            p = Plan(kind, shape, batch, FORWARD, prec, dev, lengths)
+            config = None
+            if tuned and kind == "1d":
+                from . import tune
+                config = tune.tuned_config(int(shape[0]), int(batch), _prec_code(prec), dev)
+            p = Plan(kind, shape, batch, FORWARD, prec, dev, lengths, config=config)
             _cache[key] = p
         return p
 

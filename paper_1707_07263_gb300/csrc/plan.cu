@@ -285,8 +285,16 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
 }
 
 // Planner for 1-D lengths: kind, split and kernel variants.
-static int plan_1d(fft_plan* p, int lgN) {
-  if (lgN <= 14) {
+// Planner for 1-D lengths.  cfg fields <= 0 (or tma < 0) take the defaults:
+// one on-chip pass up to 2^14 (TMA-staged for 2^9..2^12), two passes up to
+// 2^22, three passes above; split lengths as even as possible; as many
+// adjacent columns per CTA as fit 2^13 points (at most 16).
+static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
+  fft_plan_config dflt;
+  memset(&dflt, 0, sizeof(dflt));
+  dflt.tma = -1;
+  if (!cfg) cfg = &dflt;
+  if (lgN <= 14 && cfg->npass <= 1) {
     p->kind = KIND_SINGLE;
     p->lg = p->lg1 = lgN;
     p->k1 = tile_kernel(MAP_JJ, lgN, jj_cols(lgN));
@@ -296,7 +304,9 @@ static int plan_1d(fft_plan* p, int lgN) {
     if (rc) return rc;
     // Persistent TMA staging pays where several CTAs share an SM and the tile
     // is large enough to amortise the copy (measured: 2^9..2^12).
-    if (lgN >= 9 && lgN <= 12 && !env_int("GBFFT_NO_TMA", 0)) {
+    const bool want_tma =
+        cfg->tma < 0 ? (lgN >= 9 && lgN <= 12 && !env_int("GBFFT_NO_TMA", 0)) : (cfg->tma > 0 && lgN >= 1);
+    if (want_tma) {
       p->ktma = tile_kernel_tma(lgN);
       rc = prepare_kernel(p->ktma);
       if (rc) return rc;
@@ -312,21 +322,22 @@ static int plan_1d(fft_plan* p, int lgN) {
     return build_tables(p, lgN, 0, 0);
   }
   p->kind = KIND_FOURSTEP;
-  int npass = (lgN >= 23) ? 3 : 2;
+  int npass = cfg->npass >= 2 ? cfg->npass : ((lgN >= 23) ? 3 : 2);
   const int force_np = env_int("GBFFT_PASSES", 0);
-  if (force_np == 2 || force_np == 3) npass = force_np;
+  if (cfg->npass < 2 && (force_np == 2 || force_np == 3)) npass = force_np;
+  if (npass == 3 && lgN < 3) return FFT_ERR_UNSUPPORTED;
   if (p->prec != FFT_PREC_FP32) npass = 2;  // tensor-core kernels are compiled for two-pass splits
   if (npass == 2 && lgN > 28) return FFT_ERR_UNSUPPORTED;
   if (npass == 2) {
     int lg2 = (lgN + 1) / 2;
-    const int force_lg1 = env_int("GBFFT_FORCE_SPLIT", 0);
+    const int force_lg1 = cfg->lg1 > 0 ? cfg->lg1 : env_int("GBFFT_FORCE_SPLIT", 0);
     if (force_lg1 > 0 && force_lg1 < lgN && lgN - force_lg1 <= 14 && force_lg1 <= 14) lg2 = lgN - force_lg1;
     const int lg1 = lgN - lg2;
-    if (lg1 > 14 || lg2 > 14) return FFT_ERR_UNSUPPORTED;
+    if (lg1 > 14 || lg2 > 14 || lg1 < 1 || lg2 < 1) return FFT_ERR_UNSUPPORTED;
     p->lg1 = lg1;
     p->lg2 = lg2;
-    p->c1 = env_int("GBFFT_FORCE_C1", default_cols(lg1));
-    p->c2 = env_int("GBFFT_FORCE_C2", default_cols(lg2));
+    p->c1 = cfg->c1 > 0 ? cfg->c1 : env_int("GBFFT_FORCE_C1", default_cols(lg1));
+    p->c2 = cfg->c2 > 0 ? cfg->c2 : env_int("GBFFT_FORCE_C2", default_cols(lg2));
     if (p->c1 > (1 << lg2)) p->c1 = 1 << lg2;
     if (p->c2 > (1 << lg1)) p->c2 = 1 << lg1;
     p->k1 = tile_kernel(MAP_CC, lg1, p->c1);
@@ -385,15 +396,20 @@ static int plan_1d(fft_plan* p, int lgN) {
   //   B  per k1, columns of length N2 over stride N3 of the M-point
   //      row, scaled by W_M^{n3*k2}                                   ws -> ws (in place)
   //   C  rows of length N3, written to X[k1 + N1*k2 + N1*N2*k3]      ws -> out
-  const int l1 = (lgN + 2) / 3, l2 = (lgN - l1 + 1) / 2, l3 = lgN - l1 - l2;
-  if (l1 > 14 || l2 > 14 || l3 > 14 || l3 < 1) return FFT_ERR_UNSUPPORTED;
+  int l1 = (lgN + 2) / 3, l2 = (lgN - l1 + 1) / 2;
+  if (cfg->lg1 > 0) {
+    l1 = cfg->lg1;
+    l2 = cfg->lg2 > 0 ? cfg->lg2 : (lgN - l1 + 1) / 2;
+  }
+  const int l3 = lgN - l1 - l2;
+  if (l1 < 1 || l2 < 1 || l1 > 14 || l2 > 14 || l3 > 14 || l3 < 1) return FFT_ERR_UNSUPPORTED;
   p->lg1 = l1;
   p->lg2 = l2;
   p->lg3 = l3;
   const long long N = p->n, N1 = 1LL << l1, N2 = 1LL << l2, N3 = 1LL << l3, M = N2 * N3;
-  const int cA = (int)std::min<long long>(default_cols(l1), M);
-  const int cB = (int)std::min<long long>(default_cols(l2), N3);
-  const int cC = (int)std::min<long long>(default_cols(l3), N1);
+  const int cA = (int)std::min<long long>(cfg->c1 > 0 ? cfg->c1 : default_cols(l1), M);
+  const int cB = (int)std::min<long long>(cfg->c2 > 0 ? cfg->c2 : default_cols(l2), N3);
+  const int cC = (int)std::min<long long>(cfg->c3 > 0 ? cfg->c3 : default_cols(l3), N1);
   const TileKernelInfo* kA = tile_kernel(MAP_CC, l1, cA);
   const TileKernelInfo* kB = tile_kernel(MAP_CC, l2, cB);
   const TileKernelInfo* kC = tile_kernel(MAP_JC, l3, cC);
@@ -602,7 +618,7 @@ static int build_2d(fft_plan* p, int ly, int lx) {
 // ============================================================================
 extern "C" {
 
-fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec) {
+static fft_plan* create_1d(int64_t n, int64_t batch, int dir, int prec, const fft_plan_config* cfg) {
   const int lgN = ilog2_exact(n);
   if (lgN < 1 || lgN > FFT_MAX_LOG2N || batch < 1 || !valid_dir(dir) || !valid_prec(prec)) {
     set_err(FFT_ERR_INVALID_ARG);
@@ -621,7 +637,7 @@ fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec) {
   p->batch = batch;
   p->dir = dir;
   p->prec = prec;
-  int rc = plan_1d(p, lgN);
+  int rc = plan_1d(p, lgN, cfg);
   if (rc == FFT_OK && prec != FFT_PREC_FP32) rc = tc_plan_init(p);
   if (rc != FFT_OK) {
     free_plan(p);
@@ -629,6 +645,40 @@ fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec) {
     return nullptr;
   }
   return p;
+}
+
+fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec) {
+  return create_1d(n, batch, dir, prec, nullptr);
+}
+
+fft_plan* fft_plan_create_config(int64_t n, int64_t batch, int dir, int prec, const fft_plan_config* cfg) {
+  return create_1d(n, batch, dir, prec, cfg);
+}
+
+int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
+  if (!p || !out) return set_err(FFT_ERR_INVALID_ARG);
+  memset(out, 0, sizeof(*out));
+  if (p->kind == KIND_SINGLE) {
+    out->npass = 1;
+    out->lg1 = p->lg;
+    out->c1 = p->c1;
+    out->tma = p->ktma ? 1 : 0;
+  } else if (p->kind == KIND_FOURSTEP) {
+    out->npass = p->npass ? p->npass : 2;
+    out->lg1 = p->lg1;
+    out->lg2 = p->lg2;
+    if (out->npass == 3) {
+      out->c1 = p->pass[0].k->C;
+      out->c2 = p->pass[1].k->C;
+      out->c3 = p->pass[2].k->C;
+    } else {
+      out->c1 = p->c1;
+      out->c2 = p->c2;
+    }
+  } else {
+    return set_err(FFT_ERR_INVALID_ARG);
+  }
+  return FFT_OK;
 }
 
 fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int prec) {

@@ -1,0 +1,79 @@
+"""Autotune cache: the fastest plan configuration per (GPU, n, batch, prec).
+
+The search itself is native (fft_autotune in the library times every
+candidate configuration with CUDA events); this module only stores its
+answers in a JSON file so a shape is tuned once per GPU model.  The file is
+$GBFFT_TUNE_CACHE, else ~/.cache/gbfft/tune.json.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import threading
+
+import torch
+
+from . import _lib as L
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("GBFFT_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "gbfft",
+                                                                "tune.json")
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: dict) -> None:
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def key(n: int, batch: int, prec: int, device) -> str:
+    name = torch.cuda.get_device_name(device).replace(" ", "_")
+    return f"{name}|n={n}|batch={batch}|prec={prec}"
+
+
+def autotune(n: int, batch: int, prec: int = 0, device=None, iters: int = 10, stream=None) -> tuple[dict, float]:
+    """Run the native search now on scratch buffers; returns (config, microseconds)."""
+    lib = L.load()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    x = torch.randn(n * batch, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    ws = torch.empty(n * batch * 8 + 256, dtype=torch.uint8, device=dev)
+    wsp = (ws.data_ptr() + 255) & ~255
+    best = L.FftPlanConfig()
+    us = ctypes.c_float(0.0)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = lib.fft_autotune(n, batch, prec, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                          ctypes.c_void_p(wsp), n * batch * 8, ctypes.c_void_p(s.cuda_stream), iters,
+                          ctypes.byref(best), ctypes.byref(us))
+    L.check(rc, "fft_autotune")
+    return best.as_dict(), float(us.value)
+
+
+def tuned_config(n: int, batch: int, prec: int = 0, device=None, retune: bool = False) -> dict:
+    """Cached configuration for the shape, tuning it first if needed."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    k = key(n, batch, prec, dev)
+    with _lock:
+        cache = _load()
+        if k in cache and not retune:
+            return cache[k]["config"]
+        cfg, us = autotune(n, batch, prec, dev)
+        cache = _load()
+        cache[k] = {"config": cfg, "us": us}
+        _store(cache)
+        return cfg

@@ -1,0 +1,82 @@
+"""Plan configurations and the native autotuner."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1707_07263_gb300 import _lib, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load()
+
+
+def run_cfg(lib, x: np.ndarray, cfg: dict) -> np.ndarray:
+    batch, n = x.shape
+    c = _lib.FftPlanConfig.from_dict(cfg)
+    h = ctypes.c_void_p(lib.fft_plan_create_config(n, batch, 0, 0, ctypes.byref(c)))
+    assert h.value, (cfg, _lib.ERRORS.get(lib.fft_last_error()))
+    got_cfg = _lib.FftPlanConfig()
+    assert lib.fft_plan_get_config(h, ctypes.byref(got_cfg)) == 0
+    ws = lib.fft_plan_workspace_bytes(h)
+    wsb = torch.empty(max(ws, 1), dtype=torch.uint8, device="cuda")
+    if ws:
+        assert lib.fft_plan_set_workspace(h, ctypes.c_void_p(wsb.data_ptr())) == 0
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    assert lib.fft_exec(h, ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    torch.cuda.synchronize()
+    lib.fft_destroy(h)
+    return out.cpu().numpy(), got_cfg.as_dict()
+
+
+@pytest.mark.parametrize("lg,cfg", [
+    (13, {"npass": 1, "tma": 1}),
+    (14, {"npass": 1, "tma": 1}),
+    (8, {"npass": 1, "tma": 1}),
+    (11, {"npass": 1, "tma": 0}),
+    (14, {"npass": 2, "lg1": 7, "c1": 16, "c2": 16}),
+    (12, {"npass": 2, "lg1": 5, "c1": 4, "c2": 16}),
+    (10, {"npass": 2, "lg1": 3, "c1": 16, "c2": 8}),
+    (20, {"npass": 2, "lg1": 9, "c1": 16, "c2": 8}),
+    (20, {"npass": 3, "lg1": 7, "lg2": 7, "c1": 16, "c2": 8, "c3": 16}),
+    (18, {"npass": 3, "lg1": 6, "lg2": 6}),
+])
+def test_explicit_configs(lib, lg, cfg):
+    n = 1 << lg
+    x = workloads.cgauss(n, 3, seed=8000 + lg)
+    got, used = run_cfg(lib, x, cfg)
+    for k, v in cfg.items():
+        assert used[k] == v, (k, used)
+    ref = oracle.transform(x.astype(np.complex128))
+    assert oracle.rel_l2_rows(got, ref).max() <= 5e-7 * lg
+
+
+def test_unsupported_config_is_rejected(lib):
+    # a row pass of length 2^3 has no compiled kernel
+    c = _lib.FftPlanConfig.from_dict({"npass": 2, "lg1": 7})
+    assert lib.fft_plan_create_config(1 << 10, 1, 0, 0, ctypes.byref(c)) is None
+    assert lib.fft_last_error() == -6
+
+
+@pytest.mark.parametrize("lg,batch", [(12, 64), (17, 4)])
+def test_autotune_returns_a_working_config(lib, lg, batch, tmp_path, monkeypatch):
+    monkeypatch.setenv("GBFFT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_1707_07263_gb300 import tune
+    n = 1 << lg
+    cfg = tune.tuned_config(n, batch, 0)
+    assert cfg["npass"] in (1, 2, 3)
+    assert (tmp_path / "tune.json").exists()
+    x = workloads.cgauss(n, batch, seed=8100 + lg)
+    got, _ = run_cfg(lib, x, cfg)
+    assert oracle.rel_l2_rows(got, oracle.transform(x.astype(np.complex128))).max() <= 5e-7 * lg
+    # the cached answer is reused
+    assert tune.tuned_config(n, batch, 0) == cfg
