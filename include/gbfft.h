@@ -101,14 +101,17 @@ GBFFT_API int fft_exec(fft_plan* plan, const void* in, void* out, void* stream);
  * tables serve every direction); used for the adjoint in backpropagation. */
 GBFFT_API int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* stream);
 
-/* Explicit plan configuration (all fields <= 0 mean "planner default";
- * tma < 0 means default).  npass: 1 = one on-chip pass (n <= 2^14), 2 = two
- * passes N = 2^lg1 * 2^(lgN-lg1), 3 = three passes 2^lg1 * 2^lg2 * 2^lg3.
- * c1, c2, c3: adjacent transforms (columns) per CTA of each pass, 1..16.
- * tma: single pass only, 1 = persistent TMA-staged kernel, 0 = register path.
- * These are the knobs of the autotuner (fft_autotune). */
+/* Explicit plan configuration (npass, lg1, lg2, c1, c2, c3 <= 0 mean
+ * "planner default"; tma, fused < 0 mean default).  npass: 1 = one on-chip
+ * pass (n <= 2^14), 2 = two passes N = 2^lg1 * 2^(lgN-lg1), 3 = three passes
+ * 2^lg1 * 2^lg2 * 2^lg3.  c1, c2, c3: adjacent transforms (columns) per CTA of
+ * each pass, 1..16.  tma: single pass only, 1 = persistent TMA-staged kernel,
+ * 0 = register path.  fused: 1 = both passes of a two-pass split in one
+ * persistent launch that pipelines slabs of the batch through an L2-resident
+ * workspace (2^13..2^18; split and columns fixed by the kernel), 0 = one launch
+ * per pass.  These are the knobs of the autotuner (fft_autotune). */
 typedef struct fft_plan_config {
-  int npass, lg1, lg2, c1, c2, c3, tma;
+  int npass, lg1, lg2, c1, c2, c3, tma, fused;
 } fft_plan_config;
 
 /* As fft_plan_create, with an explicit configuration (NULL = defaults).

@@ -28,7 +28,7 @@ ERRORS = {
 
 class FftPlanConfig(ctypes.Structure):
     """fft_plan_config of include/gbfft.h."""
-    _fields_ = [(name, ctypes.c_int) for name in ("npass", "lg1", "lg2", "c1", "c2", "c3", "tma")]
+    _fields_ = [(name, ctypes.c_int) for name in ("npass", "lg1", "lg2", "c1", "c2", "c3", "tma", "fused")]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
@@ -37,6 +37,7 @@ class FftPlanConfig(ctypes.Structure):
     def from_dict(cls, d: dict) -> "FftPlanConfig":
         c = cls()
         c.tma = -1
+        c.fused = -1
         for k, v in d.items():
             setattr(c, k, int(v))
         return c

@@ -12,6 +12,7 @@ namespace gbfft {
 
 struct TileKernelInfo;
 struct ManyPlan;
+struct FusedPlan;
 
 // One launch of a multi-pass plan.  Buffers are named by role so a plan can
 // run on any (in, out) pair: 0 = the caller's input, 1 = the caller's output,
@@ -71,6 +72,7 @@ struct fft_plan {
   int* d_status;  // device status word (bounded waits)
 
   gbfft::ManyPlan* many;
+  gbfft::FusedPlan* fused;  // both passes in one persistent launch (fused.cu)
   int launches;
 
   // multi-pass plans (four-step with two or three passes, 2-D)

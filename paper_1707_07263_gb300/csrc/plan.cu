@@ -32,6 +32,11 @@ void many_plan_free(fft_plan* p);
 int many_exec(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s);
 int tc_plan_init(fft_plan* p);
 int tc_exec(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s);
+int fused_plan_init(fft_plan* p, int lgN, long long slab_bytes);
+void fused_plan_free(fft_plan* p);
+bool fused_supported(int lgN);
+int fused_exec(fft_plan* p, const float2* in, float2* out, int conj, float sx, float sy, int scale,
+               cudaStream_t s);
 
 thread_local int g_last_error = FFT_OK;
 
@@ -159,6 +164,7 @@ static fft_plan* new_plan() {
 static void free_plan(fft_plan* p) {
   if (!p) return;
   if (p->many) many_plan_free(p);
+  if (p->fused) fused_plan_free(p);
   if (p->ws_owned && p->ws) cudaFree(p->ws);
   if (p->d_tc) cudaFree(p->d_tc);
   if (p->d_tables) cudaFree(p->d_tables);
@@ -272,6 +278,14 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
     switch (p->kind) {
       case KIND_SINGLE: rc = exec_single(p, fin, fout, dir, s); break;
       case KIND_FOURSTEP:
+        if (p->fused) {
+          const DirXf x = dir_xf(dir, p->n);
+          rc = fused_exec(p, fin, fout, x.conj, x.scale, x.conj ? -x.scale : x.scale,
+                          (x.conj || x.scale != 1.0f) ? 1 : 0, s);
+          break;
+        }
+        rc = exec_passes(p, fin, fout, dir, s);
+        break;
       case KIND_2D: rc = exec_passes(p, fin, fout, dir, s); break;
       case KIND_MANY: rc = many_exec(p, fin, fout, dir, s); break;
       default: rc = FFT_ERR_INVALID_ARG;
@@ -293,7 +307,25 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   fft_plan_config dflt;
   memset(&dflt, 0, sizeof(dflt));
   dflt.tma = -1;
+  dflt.fused = -1;
   if (!cfg) cfg = &dflt;
+  // fused two-pass launch (fused.cu): only on request (config or
+  // GBFFT_FUSED=1) or when the autotuner measures it faster.  Measured on
+  // GB300 it keeps the intermediate in L2 (DRAM reads = input only) but loses
+  // to the single pass and to separate launches, because its 4096-point tiles
+  // are bound by per-tile latency and issue, not by DRAM traffic.
+  const int env_fused = env_int("GBFFT_FUSED", -1);
+  const bool default_fused = false;
+  const bool want_fused = fused_supported(lgN) && p->prec == FFT_PREC_FP32 &&
+                          (cfg->fused > 0 || (cfg->fused < 0 && (env_fused >= 0 ? env_fused > 0 : default_fused)));
+  if (want_fused) {
+    p->kind = KIND_FOURSTEP;
+    p->npass = 2;
+    const int lg1 = lgN / 2, lg2 = lgN - lgN / 2;
+    int rc = build_tables(p, lg1, lg2, lgN);
+    if (rc) return rc;
+    return fused_plan_init(p, lgN, (long long)env_int("GBFFT_SLAB_MB", 16) << 20);
+  }
   if (lgN <= 14 && cfg->npass <= 1) {
     p->kind = KIND_SINGLE;
     p->lg = p->lg1 = lgN;
@@ -658,6 +690,8 @@ fft_plan* fft_plan_create_config(int64_t n, int64_t batch, int dir, int prec, co
 int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
   if (!p || !out) return set_err(FFT_ERR_INVALID_ARG);
   memset(out, 0, sizeof(*out));
+  out->tma = -1;
+  out->fused = 0;
   if (p->kind == KIND_SINGLE) {
     out->npass = 1;
     out->lg1 = p->lg;
@@ -665,6 +699,7 @@ int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
     out->tma = p->ktma ? 1 : 0;
   } else if (p->kind == KIND_FOURSTEP) {
     out->npass = p->npass ? p->npass : 2;
+    out->fused = p->fused ? 1 : 0;
     out->lg1 = p->lg1;
     out->lg2 = p->lg2;
     if (out->npass == 3) {

@@ -37,6 +37,12 @@ static std::vector<fft_plan_config> candidates(int lgN) {
   fft_plan_config z;
   memset(&z, 0, sizeof(z));
   z.tma = -1;
+  z.fused = 0;
+  {
+    fft_plan_config c = z;
+    c.fused = 1;
+    v.push_back(c);  // rejected by plan creation where no fused kernel exists
+  }
   if (lgN <= 14) {
     fft_plan_config c = z;
     c.npass = 1;
@@ -86,6 +92,7 @@ extern "C" GBFFT_API int fft_autotune(int64_t n, int64_t batch, int prec, void* 
   fft_plan_config dflt;
   memset(&dflt, 0, sizeof(dflt));
   dflt.tma = -1;
+  dflt.fused = -1;
   cands.insert(cands.begin(), dflt);  // the planner's default is always a candidate
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return set_err(FFT_ERR_CUDA);
