@@ -109,9 +109,12 @@ GBFFT_API int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, v
  * 0 = register path.  fused: 1 = both passes of a two-pass split in one
  * persistent launch that pipelines slabs of the batch through an L2-resident
  * workspace (2^13..2^18; split and columns fixed by the kernel), 0 = one launch
- * per pass.  These are the knobs of the autotuner (fft_autotune). */
+ * per pass.  halves: single pass only, 2 = two CTAs per transform, each
+ * computing the even or odd outputs from a radix-2 split of the input
+ * (2^12..2^14), <= 1 = one CTA per transform.  These are the knobs of the
+ * autotuner (fft_autotune). */
 typedef struct fft_plan_config {
-  int npass, lg1, lg2, c1, c2, c3, tma, fused;
+  int npass, lg1, lg2, c1, c2, c3, tma, fused, halves;
 } fft_plan_config;
 
 /* As fft_plan_create, with an explicit configuration (NULL = defaults).

@@ -117,13 +117,11 @@ __global__ void __launch_bounds__(kFusedThreads, 3) fused_kernel(const FusedArgs
       a.in = f.A.in + (first_tr + tr) * f.N;
       a.out = slot_base + tr * f.N;
       tile_body<LG1, C1, true, true>(a, g, smem);
-      // publish the tile: the barrier orders every thread's stores before
-      // thread 0's fence, which orders them before the counter update
+      // publish the tile: every thread fences its own workspace stores, the
+      // barrier collects the CTA, then the counter moves
+      __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(f.doneA + slot, 1);
-      }
+      if (threadIdx.x == 0) atomicAdd(f.doneA + slot, 1);
     } else {
       if (threadIdx.x == 0 && !fused_wait(f.doneA + slot, fused_target(f, it.slab, f.tilesA), f.wait_budget))
         atomicExch(f.status, FFT_ERR_TIMEOUT);
@@ -135,7 +133,10 @@ __global__ void __launch_bounds__(kFusedThreads, 3) fused_kernel(const FusedArgs
       tile_body<LG2, C2, false, true>(b, g, smem);
       // every read of the slot is done once all threads pass the barrier
       __syncthreads();
-      if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(f.doneB + slot) : "memory");
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(f.doneB + slot, 1);
+      }
     }
     __syncthreads();  // s_next is published; shared memory free for the next item
     i = s_next;

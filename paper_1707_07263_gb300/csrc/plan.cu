@@ -212,6 +212,23 @@ static void set_out_xf(TileArgs& a, const DirXf& x) {
 // ---- single on-chip pass -------------------------------------------------
 static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
   const DirXf x = dir_xf(dir, p->n);
+  if (p->kdif2) {
+    // two CTAs per transform: (b, k1) computes outputs k1, k1 + 2, ...
+    TileArgs a;
+    base_args(a);
+    a.in = in;
+    a.out = out;
+    a.tw = p->tw2;  // stage table of the half length
+    a.in_bstride = a.out_bstride = p->n;
+    a.in_sn = 1;
+    a.out_sn = 2;
+    a.ncols = 1;
+    a.pre_half = p->n / 2;
+    a.pre_tw = p->pre_tw;
+    a.conj_in = x.conj;
+    set_out_xf(a, x);
+    return launch_tile(p->kdif2, a, 2 * p->batch, s);
+  }
   if (p->ktma && ((uintptr_t)in & 15) == 0) {
     // persistent TMA-staged kernel: grid = resident CTAs, tiles looped
     TileArgs a;
@@ -308,6 +325,7 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   memset(&dflt, 0, sizeof(dflt));
   dflt.tma = -1;
   dflt.fused = -1;
+  dflt.halves = 0;
   if (!cfg) cfg = &dflt;
   // fused two-pass launch (fused.cu): only on request (config or
   // GBFFT_FUSED=1) or when the autotuner measures it faster.  Measured on
@@ -336,6 +354,31 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     if (rc) return rc;
     // Persistent TMA staging pays where several CTAs share an SM and the tile
     // is large enough to amortise the copy (measured: 2^9..2^12).
+    // two CTAs per transform: measured faster at 2^13 (two 2^12 halves share an
+    // SM where one 2^13 tile cannot), slower at 2^12 and 2^14
+    const int env_halves = env_int("GBFFT_HALVES", 0);
+    const bool dflt_halves = (env_halves == 2) || (env_halves == 0 && lgN == 13);
+    const bool want_dif2 = (cfg->halves == 2 || (cfg->halves == 0 && cfg->tma < 0 && dflt_halves)) &&
+                           p->prec == FFT_PREC_FP32 && tile_kernel_dif2(lgN - 1);
+    if (want_dif2) {
+      p->kdif2 = tile_kernel_dif2(lgN - 1);
+      rc = prepare_kernel(p->kdif2);
+      if (rc) return rc;
+      const int lgs[3] = {lgN, lgN - 1, 0};
+      const int lgNs[2] = {0, 0};
+      rc = build_tables_multi(p, lgs, lgNs);
+      if (rc) return rc;
+      // W_N^n, n < N/2, in the first stage-table slot's place is not enough:
+      // allocate it beside the plan tables
+      void* t = nullptr;
+      if (cudaMalloc(&t, (size_t)(1LL << (lgN - 1)) * 8) != cudaSuccess) return FFT_ERR_ALLOC;
+      p->d_tc = t;  // freed with the plan
+      p->pre_tw = (const float2*)t;
+      if (launch_gen_power_twiddles((float2*)t, lgN, 1LL << (lgN - 1), 1, 0) != cudaSuccess ||
+          cudaStreamSynchronize(0) != cudaSuccess)
+        return FFT_ERR_CUDA;
+      return FFT_OK;
+    }
     const bool want_tma =
         cfg->tma < 0 ? (lgN >= 9 && lgN <= 12 && !env_int("GBFFT_NO_TMA", 0)) : (cfg->tma > 0 && lgN >= 1);
     if (want_tma) {
@@ -361,7 +404,11 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   if (p->prec != FFT_PREC_FP32) npass = 2;  // tensor-core kernels are compiled for two-pass splits
   if (npass == 2 && lgN > 28) return FFT_ERR_UNSUPPORTED;
   if (npass == 2) {
-    int lg2 = (lgN + 1) / 2;
+    // measured on GB300 (autotuner): 2^8-point column tiles of 16 columns win
+    // up to 2^20; beyond, the even split
+    // (tensor-core plans keep the even split their kernels are compiled for)
+    const bool fp32 = p->prec == FFT_PREC_FP32;
+    int lg2 = (fp32 && lgN >= 16 && lgN <= 20) ? lgN - 8 : (lgN + 1) / 2;
     const int force_lg1 = cfg->lg1 > 0 ? cfg->lg1 : env_int("GBFFT_FORCE_SPLIT", 0);
     if (force_lg1 > 0 && force_lg1 < lgN && lgN - force_lg1 <= 14 && force_lg1 <= 14) lg2 = lgN - force_lg1;
     const int lg1 = lgN - lg2;
@@ -369,7 +416,7 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     p->lg1 = lg1;
     p->lg2 = lg2;
     p->c1 = cfg->c1 > 0 ? cfg->c1 : env_int("GBFFT_FORCE_C1", default_cols(lg1));
-    p->c2 = cfg->c2 > 0 ? cfg->c2 : env_int("GBFFT_FORCE_C2", default_cols(lg2));
+    p->c2 = cfg->c2 > 0 ? cfg->c2 : env_int("GBFFT_FORCE_C2", fp32 && lg2 >= 10 && lg2 <= 12 ? 4 : default_cols(lg2));
     if (p->c1 > (1 << lg2)) p->c1 = 1 << lg2;
     if (p->c2 > (1 << lg1)) p->c2 = 1 << lg1;
     p->k1 = tile_kernel(MAP_CC, lg1, p->c1);
@@ -428,7 +475,9 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   //   B  per k1, columns of length N2 over stride N3 of the M-point
   //      row, scaled by W_M^{n3*k2}                                   ws -> ws (in place)
   //   C  rows of length N3, written to X[k1 + N1*k2 + N1*N2*k3]      ws -> out
-  int l1 = (lgN + 2) / 3, l2 = (lgN - l1 + 1) / 2;
+  // measured on GB300: 2^8 x 2^8 x rest up to 2^28 (rest <= 2^12)
+  int l1 = (lgN >= 23 && lgN <= 28) ? 8 : (lgN + 2) / 3;
+  int l2 = (lgN >= 23 && lgN <= 28) ? 8 : (lgN - l1 + 1) / 2;
   if (cfg->lg1 > 0) {
     l1 = cfg->lg1;
     l2 = cfg->lg2 > 0 ? cfg->lg2 : (lgN - l1 + 1) / 2;
@@ -692,11 +741,13 @@ int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
   memset(out, 0, sizeof(*out));
   out->tma = -1;
   out->fused = 0;
+  out->halves = 1;
   if (p->kind == KIND_SINGLE) {
     out->npass = 1;
     out->lg1 = p->lg;
     out->c1 = p->c1;
     out->tma = p->ktma ? 1 : 0;
+    out->halves = p->kdif2 ? 2 : 1;
   } else if (p->kind == KIND_FOURSTEP) {
     out->npass = p->npass ? p->npass : 2;
     out->fused = p->fused ? 1 : 0;

@@ -130,6 +130,12 @@ struct TileArgs {
   // Four-step twiddle multiplier: 0 = the column index g*C + c, 1 = the
   // (inner) batch index b.
   int ft_by_batch;
+  // Radix-2 decimation-in-frequency split across two CTAs (PRE == 1 passes):
+  // element n of the half-length transform k1 is
+  //   (x[n] + (-1)^k1 x[n + pre_half]) * W_{2 pre_half}^{n k1},
+  // with W_{2 pre_half}^n read from pre_tw; k1 arrives as the pass's bidx.
+  long long pre_half;
+  const float2* pre_tw;
 };
 
 template <int R>
@@ -157,7 +163,7 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 
 // One pass S of the tile: gather, twiddle, R-point DFT, scatter (with the
 // barriers that separate it from its neighbours).
-template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false>
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0>
 __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                           const TileArgs& a, const float2* gin, float2* gout,
                                           long long col0, long long bidx, const float2* epi_tab) {
@@ -191,7 +197,16 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       const bool ok = (col0 + cc[i]) < a.ncols;
       const float2* p = (OFFS ? gin + (ok ? a.col_off[cc[i]] : 0) : gin + cc[i] * a.in_sc) + (long long)jj[i] * a.in_sn;
       const long long step = (long long)LR * a.in_sn;
-      if (a.stream_in) {
+      if constexpr (PRE == 1) {
+        // (x[n] +- x[n + half]) of the two-CTA radix-2 split; the twiddle
+        // W^{n k1} is applied after the conjugation below
+        const float2* p2 = p + a.pre_half;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float2 x0 = __ldcs(p + r * step), x1 = __ldcs(p2 + r * step);
+          v[i * R + r] = bidx ? csub(x0, x1) : cadd(x0, x1);
+        }
+      } else if (a.stream_in) {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[i * R + r] = ok ? __ldcs(p + r * step) : make_float2(0.f, 0.f);
       } else {
@@ -202,6 +217,14 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
     if (a.conj_in) {
 #pragma unroll
       for (int p = 0; p < P; ++p) v[p].y = -v[p].y;
+    }
+    if constexpr (PRE == 1) {
+      if (bidx) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[i * R + r] = cmul(v[i * R + r], __ldg(a.pre_tw + jj[i] + r * LR));
+      }
     }
   } else {
 #pragma unroll
@@ -266,13 +289,13 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   }
 }
 
-template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false>
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0>
 __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                            const TileArgs& a, const float2* gin, float2* gout,
                                            long long col0, long long bidx, const float2* epi_tab) {
-  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS>(v, sm, a, gin, gout, col0, bidx, epi_tab);
+  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS, PRE>(v, sm, a, gin, gout, col0, bidx, epi_tab);
   if constexpr (S + 1 < TileCfg<LG, C, IN_CF, OUT_CF>::NST)
-    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS>(v, sm, a, gin, gout, col0, bidx, epi_tab);
+    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS, PRE>(v, sm, a, gin, gout, col0, bidx, epi_tab);
 }
 
 // One tile of a pass: tile index `tile` of the launch described by `a`, using
@@ -311,6 +334,24 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, flo
 
   float2 v[Cfg::P];
   tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS>(v, sm, a, gin, gout, col0, b, epi_tab);
+}
+
+// Two CTAs per transform of length 2^(LG+1) (radix-2 decimation in
+// frequency, Sec. 2.1's butterfly applied once across the halves):
+//   X[2 k2 + k1] = sum_n W_{N/2}^{n k2} [(x[n] + (-1)^k1 x[n + N/2]) W_N^{n k1}]
+// CTA (b, k1) computes the half-length transform of the bracket for transform
+// b and writes every other output (out_sn = 2, offset k1).  Each CTA of a
+// pair reads both halves of the input; the second read of every element is
+// usually an L2 hit.  Halving the per-CTA size lets two CTAs share an SM.
+template <int LG>
+__global__ void __launch_bounds__(TileCfg<LG, 1, false, false>::T, (LG >= 13 ? 2 : 3))
+    tile_fft_dif2_kernel(const TileArgs a) {
+  extern __shared__ float2 smem[];
+  const long long b = (long long)blockIdx.x >> 1;
+  const int k1 = blockIdx.x & 1;
+  float2 v[TileCfg<LG, 1, false, false>::P];
+  tile_stage<LG, 1, false, false, 0, false, 1>(v, smem, a, a.in + b * a.in_bstride, a.out + b * a.out_bstride + k1, 0,
+                                               k1, nullptr);
 }
 
 template <int LG, int C, bool IN_CF, bool OUT_CF>

@@ -27,6 +27,9 @@ constexpr int jj_cols(int lg) { return lg >= 12 ? 1 : (lg >= 4 ? (4096 >> lg) : 
 const TileKernelInfo* tile_kernel_tma(int lg);
 constexpr int tma_exchange_width(int lg) { return lg >= 13 ? 4 : 8; }
 
+// Two-CTA radix-2 split kernels (tile_fft_dif2_kernel) for half length 2^lg.
+const TileKernelInfo* tile_kernel_dif2(int lg);
+
 // Returns NULL when (map, lg, C) was not compiled.
 const TileKernelInfo* tile_kernel(int map, int lg, int C);
 

@@ -50,6 +50,9 @@ static std::vector<fft_plan_config> candidates(int lgN) {
     v.push_back(c);
     c.tma = 1;
     v.push_back(c);
+    c.tma = 0;
+    c.halves = 2;  // rejected where no split kernel exists
+    v.push_back(c);
   }
   if (lgN >= 10) {
     for (int lg1 = lgN / 2 - 2; lg1 <= (lgN + 1) / 2 + 2; ++lg1) {

@@ -3,7 +3,12 @@
 The search itself is native (fft_autotune in the library times every
 candidate configuration with CUDA events); this module only stores its
 answers in a JSON file so a shape is tuned once per GPU model.  The file is
-$GBFFT_TUNE_CACHE, else ~/.cache/gbfft/tune.json.
+$GBFFT_TUNE_CACHE, else ~/.cache/gbfft/tune.json; when a shape is missing
+there, the results shipped with the package (tune_shipped.json, measured on
+GB300) are used before tuning anew.
+
+Command line (tunes shapes and writes them to a cache file):
+    python -m paper_1707_07263_gb300.tune --out FILE n:batch [n:batch ...]
 """
 from __future__ import annotations
 
@@ -24,9 +29,12 @@ def cache_path() -> str:
                                                                 "tune.json")
 
 
-def _load() -> dict:
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_shipped.json")
+
+
+def _load(path: str | None = None) -> dict:
     try:
-        with open(cache_path()) as f:
+        with open(path or cache_path()) as f:
             return json.load(f)
     except (OSError, ValueError):
         return {}
@@ -72,8 +80,34 @@ def tuned_config(n: int, batch: int, prec: int = 0, device=None, retune: bool = 
         cache = _load()
         if k in cache and not retune:
             return cache[k]["config"]
+        shipped = _load(SHIPPED)
+        if k in shipped and not retune:
+            return shipped[k]["config"]
         cfg, us = autotune(n, batch, prec, dev)
         cache = _load()
         cache[k] = {"config": cfg, "us": us}
         _store(cache)
         return cfg
+
+
+def main(argv=None) -> None:
+    import argparse
+    ap = argparse.ArgumentParser(description="tune plan configurations and store them")
+    ap.add_argument("--out", required=True, help="cache file to write (merged with its contents)")
+    ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("shapes", nargs="+", help="n:batch pairs")
+    args = ap.parse_args(argv)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = _load(args.out)
+    for sh in args.shapes:
+        n, b = (int(v) for v in sh.split(":"))
+        cfg, us = autotune(n, b, 0, dev, iters=args.iters)
+        out[key(n, b, 0, dev)] = {"config": cfg, "us": us}
+        print(f"{sh}: {cfg} {us:.1f} us", flush=True)
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    with open(args.out, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main()

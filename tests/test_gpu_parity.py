@@ -105,6 +105,7 @@ def test_single_pass_directions(lib, lg, d):
 def test_single_pass_register_path(lib, monkeypatch, lg):
     """The non-persistent kernel (no TMA staging) gives the same result."""
     monkeypatch.setenv("GBFFT_NO_TMA", "1")
+    monkeypatch.setenv("GBFFT_HALVES", "1")
     n = 1 << lg
     x = workloads.cgauss(n, 11, seed=6000 + lg)
     got = run_1d(lib, x, 1)

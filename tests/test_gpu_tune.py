@@ -49,6 +49,9 @@ def run_cfg(lib, x: np.ndarray, cfg: dict) -> np.ndarray:
     (20, {"npass": 2, "lg1": 9, "c1": 16, "c2": 8}),
     (20, {"npass": 3, "lg1": 7, "lg2": 7, "c1": 16, "c2": 8, "c3": 16}),
     (18, {"npass": 3, "lg1": 6, "lg2": 6}),
+    (12, {"npass": 1, "halves": 2}),
+    (13, {"npass": 1, "halves": 2}),
+    (14, {"npass": 1, "halves": 2}),
 ])
 def test_explicit_configs(lib, lg, cfg):
     n = 1 << lg
@@ -58,6 +61,26 @@ def test_explicit_configs(lib, lg, cfg):
         assert used[k] == v, (k, used)
     ref = oracle.transform(x.astype(np.complex128))
     assert oracle.rel_l2_rows(got, ref).max() <= 5e-7 * lg
+
+
+@pytest.mark.parametrize("lg", [13, 14])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_two_cta_split_directions(lib, lg, d):
+    n = 1 << lg
+    x = workloads.uniform(n, 5, seed=8200 + lg + d)
+    c = _lib.FftPlanConfig.from_dict({"npass": 1, "halves": 2})
+    h = ctypes.c_void_p(lib.fft_plan_create_config(n, 5, d, 0, ctypes.byref(c)))
+    assert h.value
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    assert lib.fft_exec(h, ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    torch.cuda.synchronize()
+    lib.fft_destroy(h)
+    x64 = x.astype(np.complex128)
+    ref = {1: oracle.fft(x64, oracle.INVERSE), 2: oracle.fft(x64, oracle.ADJOINT),
+           3: oracle.fft(x64, oracle.FORWARD) / n}[d]
+    assert oracle.rel_l2_rows(out.cpu().numpy(), ref).max() <= 5e-7 * lg
 
 
 def test_unsupported_config_is_rejected(lib):
