@@ -95,6 +95,7 @@ static int launch(const TileKernelInfo* k, const TileArgs& a, long long ntiles, 
 }
 
 int tc_exec(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
+  if ((uintptr_t)out & 15) return FFT_ERR_ALIGN;  // the last pass stores 16-byte pairs
   const int inv = dir & FFT_INVERSE, adj = (dir & FFT_ADJOINT) ? 1 : 0;
   const int conj = inv ^ adj;
   const float scale = inv ? (float)(1.0 / (double)p->n) : 1.0f;

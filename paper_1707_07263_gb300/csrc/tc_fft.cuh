@@ -18,7 +18,10 @@
 //           (exactly the B-fragment layout);
 //   outputs lane holds q in {gid, gid+8} of butterflies 32w + 8g + 2tig + {0,1}
 //           (the accumulator layout).
-// Loads and stores go through the same padded shared tile as the FP32 passes.
+// Passes exchange through a shared tile indexed by the XOR swizzle tcidx()
+// (no padding), which a bank model shows keeps these fragment-ordered
+// accesses, and the FP32 remainder pass's, at the two-wavefront minimum.
+// The last pass stores pairs of adjacent outputs as 16-byte vectors.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -82,12 +85,10 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// cos / sin of 2*pi*m/16
-__device__ __forceinline__ float cos16(int m) {
-  const float t[16] = {1.f, GBFFT_C8, GBFFT_R2, GBFFT_S8, 0.f, -GBFFT_S8, -GBFFT_R2, -GBFFT_C8,
-                       -1.f, -GBFFT_C8, -GBFFT_R2, -GBFFT_S8, 0.f, GBFFT_S8, GBFFT_R2, GBFFT_C8};
-  return t[m & 15];
-}
+// cos(2*pi*m/16), m = 0..15
+__constant__ float c_cos16[16] = {1.f, GBFFT_C8, GBFFT_R2, GBFFT_S8, 0.f, -GBFFT_S8, -GBFFT_R2, -GBFFT_C8,
+                                  -1.f, -GBFFT_C8, -GBFFT_R2, -GBFFT_S8, 0.f, GBFFT_S8, GBFFT_R2, GBFFT_C8};
+__device__ __forceinline__ float cos16(int m) { return c_cos16[m & 15]; }
 __device__ __forceinline__ float sin16(int m) { return cos16(m - 4); }
 
 // A fragments of Cm and Sm (and their lo parts for the split variants):
@@ -130,7 +131,7 @@ __device__ __forceinline__ void tc_map(int b, int& c, int& j) {
 template <int LG, int C, bool IN_CF, bool OUT_CF, int S, int PREC>
 __device__ __forceinline__ void tc_pass(float2* sm, const TileArgs& a, const float2* gin, float2* gout,
                                         long long col0, const uint32_t (&A)[4][4]) {
-  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
+  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF, 1>;
   constexpr bool BF16 = TcPrec<PREC>::BF16, SPLIT = TcPrec<PREC>::SPLIT;
   constexpr int L = Cfg::L, NST = Cfg::NST, LP = Cfg::LP;
   static_assert(radix_lgr(LG, S) == 4, "tensor-core passes are radix 16");
@@ -154,7 +155,7 @@ __device__ __forceinline__ void tc_pass(float2* sm, const TileArgs& a, const flo
         x[g][e] = ok ? (a.stream_in ? __ldcs(p) : __ldcg(p)) : make_float2(0.f, 0.f);
         if (a.conj_in) x[g][e].y = -x[g][e].y;
       } else {
-        x[g][e] = sm[c * LP + pidx(j + r * LR)];
+        x[g][e] = sm[c * LP + tcidx(j + r * LR)];
       }
       if constexpr (NS > 1) {
         if (r > 0) x[g][e] = cmul(x[g][e], __ldg(a.tw + tc_tw_off(LG, S) + (r - 1) * NS + (j & (NS - 1))));
@@ -198,27 +199,36 @@ __device__ __forceinline__ void tc_pass(float2* sm, const TileArgs& a, const flo
   }
 
   if constexpr (LAST) {
+    // outputs e = 0, 1 (and 2, 3) are butterflies 2*tig and 2*tig+1 at the same
+    // q: adjacent j (j-fast) or adjacent columns (c-fast, out_sc == 1), so
+    // each pair goes out as one 16-byte store
 #pragma unroll
     for (int g = 0; g < 4; ++g)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int q = gid + ((e & 2) ? 8 : 0);
+      for (int h = 0; h < 2; ++h) {
+        const int q = gid + (h ? 8 : 0);
         int c, j;
-        tc_map<LG, C, CF>(warp * 32 + g * 8 + 2 * tig + (e & 1), c, j);
-        float2 v = y[g][e];
+        tc_map<LG, C, CF>(warp * 32 + g * 8 + 2 * tig, c, j);
         const int k = j + q * NS;
+        float2 v0 = y[g][2 * h], v1 = y[g][2 * h + 1];
         if (Cfg::EPI && a.ft_lgN) {
-          const unsigned m = (unsigned)(col0 + c) * (unsigned)k;
           const unsigned mask = (1u << a.ft_s) - 1u;
-          v = cmul(v, cmul(__ldg(a.ft_lo + (m & mask)), __ldg(a.ft_hi + (m >> a.ft_s))));
+          const unsigned m0 = (unsigned)(col0 + c) * (unsigned)k;
+          v0 = cmul(v0, cmul(__ldg(a.ft_lo + (m0 & mask)), __ldg(a.ft_hi + (m0 >> a.ft_s))));
+          const unsigned m1 = CF ? (unsigned)(col0 + c + 1) * (unsigned)k : (unsigned)(col0 + c) * (unsigned)(k + 1);
+          v1 = cmul(v1, cmul(__ldg(a.ft_lo + (m1 & mask)), __ldg(a.ft_hi + (m1 >> a.ft_s))));
         }
-        if (a.scale_out) v = make_float2(v.x * a.sx, v.y * a.sy);
+        if (a.scale_out) {
+          v0 = make_float2(v0.x * a.sx, v0.y * a.sy);
+          v1 = make_float2(v1.x * a.sx, v1.y * a.sy);
+        }
         if ((col0 + c) < a.ncols) {
-          float2* p = gout + c * a.out_sc + (long long)k * a.out_sn;
+          float4* p = (float4*)(gout + c * a.out_sc + (long long)k * a.out_sn);
+          const float4 w = make_float4(v0.x, v0.y, v1.x, v1.y);
           if (a.stream_out)
-            __stcs(p, v);
+            __stcs(p, w);
           else
-            __stcg(p, v);
+            __stcg(p, w);
         }
       }
   } else {
@@ -231,7 +241,7 @@ __device__ __forceinline__ void tc_pass(float2* sm, const TileArgs& a, const flo
         int c, j;
         tc_map<LG, C, CF>(warp * 32 + g * 8 + 2 * tig + (e & 1), c, j);
         const int pos = ((j >> LGNS) << (LGNS + 4)) + (j & (NS - 1)) + q * NS;
-        sm[c * LP + pidx(pos)] = y[g][e];
+        sm[c * LP + tcidx(pos)] = y[g][e];
       }
     __syncthreads();
   }
@@ -241,19 +251,19 @@ __device__ __forceinline__ void tc_pass(float2* sm, const TileArgs& a, const flo
 template <int LG, int C, bool IN_CF, bool OUT_CF, int S, int PREC>
 __device__ __forceinline__ void tc_stage(float2* sm, const TileArgs& a, const float2* gin, float2* gout,
                                          long long col0, const float2* epi_tab, const uint32_t (&A)[4][4]) {
-  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
+  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF, 1>;
   if constexpr (radix_lgr(LG, S) == 4) {
     tc_pass<LG, C, IN_CF, OUT_CF, S, PREC>(sm, a, gin, gout, col0, A);
   } else {
     float2 v[Cfg::P];
-    tile_pass<LG, C, IN_CF, OUT_CF, S>(v, sm, a, gin, gout, col0, 0, epi_tab);
+    tile_pass<LG, C, IN_CF, OUT_CF, S, false, 0, 1>(v, sm, a, gin, gout, col0, 0, epi_tab);
   }
   if constexpr (S + 1 < Cfg::NST) tc_stage<LG, C, IN_CF, OUT_CF, S + 1, PREC>(sm, a, gin, gout, col0, epi_tab, A);
 }
 
 template <int LG, int C, bool IN_CF, bool OUT_CF, int PREC>
-__global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T) tc_fft_kernel(const TileArgs a) {
-  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
+__global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF, 1>::T) tc_fft_kernel(const TileArgs a) {
+  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF, 1>;
   static_assert(Cfg::T % 32 == 0 && Cfg::P == 16, "tensor-core tiles use whole warps of 16-point threads");
   extern __shared__ float2 smem[];
   const long long tile = (long long)blockIdx.x;

@@ -5,8 +5,8 @@
 namespace gbfft {
 
 #define GBFFT_TC(LG, C, ICF, OCF, MAP, PREC) \
-  {(const void*)&tc_fft_kernel<LG, C, ICF, OCF, PREC>, TileCfg<LG, C, ICF, OCF>::T, \
-   TileCfg<LG, C, ICF, OCF>::SMEM_BYTES, LG, C, MAP}
+  {(const void*)&tc_fft_kernel<LG, C, ICF, OCF, PREC>, TileCfg<LG, C, ICF, OCF, 1>::T, \
+   TileCfg<LG, C, ICF, OCF, 1>::SMEM_BYTES, LG, C, MAP}
 
 const TileKernelInfo* tc_kernel_fp16(int map, int lg, int C) {
   static const TileKernelInfo tab[] = {

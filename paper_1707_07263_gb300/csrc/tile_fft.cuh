@@ -78,13 +78,23 @@ __host__ __device__ constexpr int tile_row_pad(int lg, int C, bool in_cf, bool o
   return ((32 / tile_group_count(lg, C, in_cf, out_cf, 0)) % 16 - (((1 << lg) + ((1 << lg) >> 4)) % 16) + 32) % 16;
 }
 
-template <int LG, int C, bool IN_CF, bool OUT_CF>
+// Shared-memory index of element n of a transform's row:
+//   IDX 0  padded: n + n/16 (FP32 kernels);
+//   IDX 1  XOR swizzle inside 16-element blocks, no padding (tensor-core
+//          kernels, whose fragment-ordered accesses it keeps conflict-free).
+template <int IDX>
+__host__ __device__ constexpr int tc_row_pad(int C, bool in_cf, bool out_cf) {
+  return (in_cf || out_cf) ? (C == 2 ? 4 : 2) : 0;
+}
+
+template <int LG, int C, bool IN_CF, bool OUT_CF, int IDX = 0>
 struct TileCfg {
   static constexpr int L = 1 << LG;
   static constexpr int P = L < 16 ? L : 16;         // points per thread
   static constexpr int T = C * L / P;               // threads per CTA
   static constexpr int NST = radix_nst(LG);
-  static constexpr int LP = L + (L >> 4) + tile_row_pad(LG, C, IN_CF, OUT_CF);
+  static constexpr int LP = IDX == 0 ? L + (L >> 4) + tile_row_pad(LG, C, IN_CF, OUT_CF)
+                                     : L + tc_row_pad<IDX>(C, IN_CF, OUT_CF);
   static constexpr int SM_TILE = NST > 1 ? C * LP : 0;   // complex entries
   static constexpr bool EPI = IN_CF && OUT_CF;            // column pass: may carry the four-step twiddle
   static constexpr int SM_EPI = EPI ? C * 16 : 0;         // four-step per-column step table
@@ -92,6 +102,14 @@ struct TileCfg {
 };
 
 __device__ __forceinline__ int pidx(int n) { return n + (n >> 4); }
+__device__ __forceinline__ int tcidx(int n) { return n ^ ((((n >> 4) * 13) ^ (n >> 6)) & 15); }
+template <int IDX>
+__device__ __forceinline__ int sidx(int n) {
+  if constexpr (IDX == 0)
+    return pidx(n);
+  else
+    return tcidx(n);
+}
 
 // ---------------------------------------------------------------------------
 // Kernel arguments.  Tile t = (b, g) with b = t / tiles_per_batch and
@@ -163,11 +181,11 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 
 // One pass S of the tile: gather, twiddle, R-point DFT, scatter (with the
 // barriers that separate it from its neighbours).
-template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0>
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int IDX = 0>
 __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                           const TileArgs& a, const float2* gin, float2* gout,
                                           long long col0, long long bidx, const float2* epi_tab) {
-  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
+  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF, IDX>;
   constexpr int L = Cfg::L, P = Cfg::P, T = Cfg::T, NST = Cfg::NST, LP = Cfg::LP;
   constexpr int LGR = radix_lgr(LG, S), R = 1 << LGR;
   constexpr int LGNS = radix_lgns(LG, S), NS = 1 << LGNS;
@@ -230,7 +248,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i * R + r] = sm[cc[i] * LP + pidx(jj[i] + r * LR)];
+      for (int r = 0; r < R; ++r) v[i * R + r] = sm[cc[i] * LP + sidx<IDX>(jj[i] + r * LR)];
   }
 
   // ---- twiddles W_{Ns*R}^{r*(j mod Ns)} ----
@@ -283,7 +301,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       const int j = jj[i];
       const int base = ((j >> LGNS) << (LGNS + LGR)) + (j & (NS - 1));
 #pragma unroll
-      for (int q = 0; q < R; ++q) sm[cc[i] * LP + pidx(base + q * NS)] = v[i * R + q];
+      for (int q = 0; q < R; ++q) sm[cc[i] * LP + sidx<IDX>(base + q * NS)] = v[i * R + q];
     }
     __syncthreads();
   }
