@@ -352,12 +352,13 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     p->launches = 1;
     int rc = prepare_kernel(p->k1);
     if (rc) return rc;
-    // Persistent TMA staging pays where several CTAs share an SM and the tile
-    // is large enough to amortise the copy (measured: 2^9..2^12).
-    // two CTAs per transform: measured faster at 2^13 (two 2^12 halves share an
-    // SM where one 2^13 tile cannot), slower at 2^12 and 2^14
+    // Two CTAs per transform (radix-2 split) is an autotuner option: with the
+    // linear shared-memory addressing the one-CTA pass measures faster at
+    // 2^12..2^14 on GB300.  Persistent TMA staging pays where several CTAs
+    // share an SM and the tile amortises the copy (measured: 2^9..2^11; at
+    // 2^12 the register path is as fast).
     const int env_halves = env_int("GBFFT_HALVES", 0);
-    const bool dflt_halves = (env_halves == 2) || (env_halves == 0 && lgN == 13);
+    const bool dflt_halves = env_halves == 2;
     const bool want_dif2 = (cfg->halves == 2 || (cfg->halves == 0 && cfg->tma < 0 && dflt_halves)) &&
                            p->prec == FFT_PREC_FP32 && tile_kernel_dif2(lgN - 1);
     if (want_dif2) {
@@ -380,7 +381,7 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
       return FFT_OK;
     }
     const bool want_tma =
-        cfg->tma < 0 ? (lgN >= 9 && lgN <= 12 && !env_int("GBFFT_NO_TMA", 0)) : (cfg->tma > 0 && lgN >= 1);
+        cfg->tma < 0 ? (lgN >= 9 && lgN <= 11 && !env_int("GBFFT_NO_TMA", 0)) : (cfg->tma > 0 && lgN >= 1);
     if (want_tma) {
       p->ktma = tile_kernel_tma(lgN);
       rc = prepare_kernel(p->ktma);

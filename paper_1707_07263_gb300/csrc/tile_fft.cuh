@@ -102,6 +102,12 @@ struct TileCfg {
 };
 
 __device__ __forceinline__ int pidx(int n) { return n + (n >> 4); }
+// pidx of a compile-time offset.  For every pass, pidx(base + d) ==
+// pidx(base) + pidx_c(d) holds for the element offsets d = r*L/R (reads) and
+// d = q*Ns (writes): d is a multiple of 16, or base's low four bits plus d stay
+// inside one 16-block.  The shared-memory address of each of a butterfly's R
+// elements is then one base register plus an immediate.
+__host__ __device__ constexpr int pidx_c(int n) { return n + (n >> 4); }
 __device__ __forceinline__ int tcidx(int n) { return n ^ ((((n >> 4) * 13) ^ (n >> 6)) & 15); }
 template <int IDX>
 __device__ __forceinline__ int sidx(int n) {
@@ -213,8 +219,11 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const bool ok = (col0 + cc[i]) < a.ncols;
-      const float2* p = (OFFS ? gin + (ok ? a.col_off[cc[i]] : 0) : gin + cc[i] * a.in_sc) + (long long)jj[i] * a.in_sn;
-      const long long step = (long long)LR * a.in_sn;
+      // a j-fast input is always a contiguous row (in_sn == 1 for every plan
+      // that uses it), so its element offsets are compile-time constants
+      const long long isn = IN_CF ? a.in_sn : 1;
+      const float2* p = (OFFS ? gin + (ok ? a.col_off[cc[i]] : 0) : gin + cc[i] * a.in_sc) + (long long)jj[i] * isn;
+      const long long step = (long long)LR * isn;
       if constexpr (PRE == 1) {
         // (x[n] +- x[n + half]) of the two-CTA radix-2 split; the twiddle
         // W^{n k1} is applied after the conjugation below
@@ -246,9 +255,16 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < NB; ++i)
+    for (int i = 0; i < NB; ++i) {
+      if constexpr (IDX == 0) {
+        const float2* rp = sm + cc[i] * LP + pidx(jj[i]);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i * R + r] = sm[cc[i] * LP + sidx<IDX>(jj[i] + r * LR)];
+        for (int r = 0; r < R; ++r) v[i * R + r] = rp[pidx_c(r * LR)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i * R + r] = sm[cc[i] * LP + sidx<IDX>(jj[i] + r * LR)];
+      }
+    }
   }
 
   // ---- twiddles W_{Ns*R}^{r*(j mod Ns)} ----
@@ -284,8 +300,11 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       for (int q = 0; q < R; ++q) v[q] = make_float2(v[q].x * a.sx, v[q].y * a.sy);
     }
     if (ok) {
-      float2* p = (OFFS ? gout + a.col_off[c] : gout + c * a.out_sc) + (long long)j * a.out_sn;
-      const long long step = (long long)NS * a.out_sn;
+      // a j-fast output is contiguous (out_sn == 1), or every other element
+      // for the two-CTA split (PRE == 1); c-fast outputs use the runtime stride
+      const long long osn = OUT_CF ? a.out_sn : (PRE == 1 ? 2 : 1);
+      float2* p = (OFFS ? gout + a.col_off[c] : gout + c * a.out_sc) + (long long)j * osn;
+      const long long step = (long long)NS * osn;
       if (a.stream_out) {
 #pragma unroll
         for (int q = 0; q < R; ++q) __stcs(p + q * step, v[q]);
@@ -300,8 +319,14 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
     for (int i = 0; i < NB; ++i) {
       const int j = jj[i];
       const int base = ((j >> LGNS) << (LGNS + LGR)) + (j & (NS - 1));
+      if constexpr (IDX == 0) {
+        float2* wp = sm + cc[i] * LP + pidx(base);
 #pragma unroll
-      for (int q = 0; q < R; ++q) sm[cc[i] * LP + sidx<IDX>(base + q * NS)] = v[i * R + q];
+        for (int q = 0; q < R; ++q) wp[pidx_c(q * NS)] = v[i * R + q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) sm[cc[i] * LP + sidx<IDX>(base + q * NS)] = v[i * R + q];
+      }
     }
     __syncthreads();
   }

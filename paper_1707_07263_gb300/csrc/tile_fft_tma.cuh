@@ -146,16 +146,18 @@ __device__ __forceinline__ void tma_exchange(float2* v, void* Xraw, int tid) {
     for (int i = 0; i < NB0; ++i) {
       int c, j;
       tma_bfly<LG, C, S>(tid, i, c, j);
+      float2* wp = X + c * LP + pidx(tma_out_pos<LG, S>(j, 0));
 #pragma unroll
-      for (int q = 0; q < R0; ++q) X[c * LP + pidx(tma_out_pos<LG, S>(j, q))] = v[i * R0 + q];
+      for (int q = 0; q < R0; ++q) wp[pidx_c(q * (1 << radix_lgns(LG, S)))] = v[i * R0 + q];
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < NB1; ++i) {
       int c, j;
       tma_bfly<LG, C, S + 1>(tid, i, c, j);
+      const float2* rp = X + c * LP + pidx(j);
 #pragma unroll
-      for (int r = 0; r < R1; ++r) v[i * R1 + r] = X[c * LP + pidx(j + r * LR1)];
+      for (int r = 0; r < R1; ++r) v[i * R1 + r] = rp[pidx_c(r * LR1)];
     }
   } else {
     static_assert(C == 1, "split exchange is compiled for one transform per CTA");
