@@ -105,8 +105,9 @@ GBFFT_API int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, v
  * "planner default"; tma, fused < 0 mean default).  npass: 1 = one on-chip
  * pass (n <= 2^14), 2 = two passes N = 2^lg1 * 2^(lgN-lg1), 3 = three passes
  * 2^lg1 * 2^lg2 * 2^lg3.  c1, c2, c3: adjacent transforms (columns) per CTA of
- * each pass, 1..16.  tma: single pass only, 1 = persistent TMA-staged kernel,
- * 0 = register path.  fused: 1 = both passes of a two-pass split in one
+ * each pass, 1..64.  tma: 1 = persistent TMA-staged kernels (single pass:
+ * cp.async.bulk of contiguous tiles; multi-pass: column passes staged by
+ * tensor TMA boxes), 0 = register path.  fused: 1 = both passes of a two-pass split in one
  * persistent launch that pipelines slabs of the batch through an L2-resident
  * workspace (2^13..2^18; split and columns fixed by the kernel), 0 = one launch
  * per pass.  halves: single pass only, 2 = two CTAs per transform, each

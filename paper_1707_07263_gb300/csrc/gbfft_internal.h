@@ -23,6 +23,8 @@ struct PassDesc {
   TileArgs a;
   int in_role, out_role;
   long long ntiles;
+  const TileKernelInfo* kcol;  // tensor-TMA variant of a column pass (or NULL)
+  int col_grid;                // its resident-CTA grid
 };
 constexpr int kMaxPasses = 4;
 

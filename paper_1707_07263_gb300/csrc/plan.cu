@@ -265,6 +265,34 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
   return launch_tile(p->k1, a, a.tiles_per_batch, s);
 }
 
+// Attach the tensor-TMA variant to every column pass that has one, when
+// asked for (config tma = 1 on a multi-pass plan, or GBFFT_COLTMA=1).
+// Measured on GB300 it is correct but no faster than the register path for
+// these strided tiles (their DRAM pattern, not load latency, limits them), so
+// it is off by default and left to the autotuner.  Whether a given exec can
+// use it (alignment, strides) is decided per call.
+static int attach_coltma(fft_plan* p, bool want) {
+  if (!want && !env_int("GBFFT_COLTMA", 0)) return FFT_OK;
+  for (int i = 0; i < p->npass; ++i) {
+    PassDesc& d = p->pass[i];
+    if (d.k->map != MAP_CC) continue;
+    const TileKernelInfo* kc = tile_kernel_coltma(d.k->lg, d.k->C);
+    if (!kc) continue;
+    int rc = prepare_kernel(kc);
+    if (rc) return rc;
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc->fn, kc->threads, (size_t)kc->smem_bytes) !=
+            cudaSuccess ||
+        per_sm < 1)
+      return FFT_ERR_CUDA;
+    d.kcol = kc;
+    d.col_grid = per_sm * sms;
+  }
+  return FFT_OK;
+}
+
 // ---- multi-pass plans: run the pass list ------------------------------------
 static int exec_passes(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
   const DirXf x = dir_xf(dir, p->n);
@@ -277,7 +305,9 @@ static int exec_passes(fft_plan* p, const float2* in, float2* out, int dir, cuda
     a.out = roles[d.out_role];
     if (i == 0) a.conj_in = x.conj;
     if (i == p->npass - 1) set_out_xf(a, x);
-    const int rc = launch_tile(d.k, a, d.ntiles, s);
+    const int rc = (d.kcol && coltma_usable(d.kcol, a, a.in))
+                       ? coltma_launch(d.kcol, a, d.ntiles, d.col_grid, p->d_status, s)
+                       : launch_tile(d.k, a, d.ntiles, s);
     if (rc) return rc;
   }
   return FFT_OK;
@@ -469,7 +499,7 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     p->npass = 2;
     p->launches = 2;
     p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
-    return FFT_OK;
+    return attach_coltma(p, cfg->tma > 0);
   }
   // three passes, N = N1 * N2 * N3 (M = N2 * N3):
   //   A  columns of length N1 over stride M, scaled by W_N^{m*k1}     in -> ws
@@ -567,7 +597,7 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   p->npass = 3;
   p->launches = 3;
   p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
-  return FFT_OK;
+  return attach_coltma(p, cfg->tma > 0);
 }
 
 // 2-D plan (Sec. 2.3.2: rows, then columns).  Rows: one on-chip pass over all
@@ -626,7 +656,7 @@ static int build_2d(fft_plan* p, int ly, int lx) {
     p->npass = 2;
     p->launches = 2;
     p->ws_bytes = 0;
-    return FFT_OK;
+    return attach_coltma(p, false);
   }
   const int ly1 = ly / 2, ly2 = ly - ly1;
   const long long Y1 = 1LL << ly1, Y2 = 1LL << ly2;
@@ -690,7 +720,7 @@ static int build_2d(fft_plan* p, int ly, int lx) {
   p->npass = 3;
   p->launches = 3;
   p->ws_bytes = (size_t)img * (size_t)p->batch * 8;
-  return FFT_OK;
+  return attach_coltma(p, false);
 }
 
 }  // namespace gbfft
@@ -752,6 +782,7 @@ int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
   } else if (p->kind == KIND_FOURSTEP) {
     out->npass = p->npass ? p->npass : 2;
     out->fused = p->fused ? 1 : 0;
+    out->tma = (!p->fused && p->pass[0].kcol) ? 1 : 0;
     out->lg1 = p->lg1;
     out->lg2 = p->lg2;
     if (out->npass == 3) {

@@ -224,7 +224,12 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       const long long isn = IN_CF ? a.in_sn : 1;
       const float2* p = (OFFS ? gin + (ok ? a.col_off[cc[i]] : 0) : gin + cc[i] * a.in_sc) + (long long)jj[i] * isn;
       const long long step = (long long)LR * isn;
-      if constexpr (PRE == 1) {
+      if constexpr (PRE == 2) {
+        // column tile already staged in shared memory by a tensor TMA copy,
+        // laid out [n][c] (gin points at it)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i * R + r] = gin[(jj[i] + r * LR) * C + cc[i]];
+      } else if constexpr (PRE == 1) {
         // (x[n] +- x[n + half]) of the two-CTA radix-2 split; the twiddle
         // W^{n k1} is applied after the conjugation below
         const float2* p2 = p + a.pre_half;

@@ -30,16 +30,22 @@ const TileKernelInfo* tile_kernel_cc_a(int lg, int C) {
       GBFFT_TK(5, 4, true, true, MAP_CC),
       GBFFT_TK(5, 8, true, true, MAP_CC),
       GBFFT_TK(5, 16, true, true, MAP_CC),
+      GBFFT_TK(5, 32, true, true, MAP_CC),
+      GBFFT_TK(5, 64, true, true, MAP_CC),
       GBFFT_TK(6, 1, true, true, MAP_CC),
       GBFFT_TK(6, 2, true, true, MAP_CC),
       GBFFT_TK(6, 4, true, true, MAP_CC),
       GBFFT_TK(6, 8, true, true, MAP_CC),
       GBFFT_TK(6, 16, true, true, MAP_CC),
+      GBFFT_TK(6, 32, true, true, MAP_CC),
+      GBFFT_TK(6, 64, true, true, MAP_CC),
       GBFFT_TK(7, 1, true, true, MAP_CC),
       GBFFT_TK(7, 2, true, true, MAP_CC),
       GBFFT_TK(7, 4, true, true, MAP_CC),
       GBFFT_TK(7, 8, true, true, MAP_CC),
       GBFFT_TK(7, 16, true, true, MAP_CC),
+      GBFFT_TK(7, 32, true, true, MAP_CC),
+      GBFFT_TK(7, 64, true, true, MAP_CC),
   };
   for (const TileKernelInfo& k : tab)
     if (k.lg == lg && k.C == C) return &k;

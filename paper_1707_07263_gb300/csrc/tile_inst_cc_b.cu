@@ -10,11 +10,14 @@ const TileKernelInfo* tile_kernel_cc_b(int lg, int C) {
       GBFFT_TK(8, 4, true, true, MAP_CC),
       GBFFT_TK(8, 8, true, true, MAP_CC),
       GBFFT_TK(8, 16, true, true, MAP_CC),
+      GBFFT_TK(8, 32, true, true, MAP_CC),
+      GBFFT_TK(8, 64, true, true, MAP_CC),
       GBFFT_TK(9, 1, true, true, MAP_CC),
       GBFFT_TK(9, 2, true, true, MAP_CC),
       GBFFT_TK(9, 4, true, true, MAP_CC),
       GBFFT_TK(9, 8, true, true, MAP_CC),
       GBFFT_TK(9, 16, true, true, MAP_CC),
+      GBFFT_TK(9, 32, true, true, MAP_CC),
       GBFFT_TK(10, 1, true, true, MAP_CC),
       GBFFT_TK(10, 2, true, true, MAP_CC),
       GBFFT_TK(10, 4, true, true, MAP_CC),

@@ -10,21 +10,29 @@ const TileKernelInfo* tile_kernel_jc_a(int lg, int C) {
       GBFFT_TK(5, 4, false, true, MAP_JC),
       GBFFT_TK(5, 8, false, true, MAP_JC),
       GBFFT_TK(5, 16, false, true, MAP_JC),
+      GBFFT_TK(5, 32, false, true, MAP_JC),
+      GBFFT_TK(5, 64, false, true, MAP_JC),
       GBFFT_TK(6, 1, false, true, MAP_JC),
       GBFFT_TK(6, 2, false, true, MAP_JC),
       GBFFT_TK(6, 4, false, true, MAP_JC),
       GBFFT_TK(6, 8, false, true, MAP_JC),
       GBFFT_TK(6, 16, false, true, MAP_JC),
+      GBFFT_TK(6, 32, false, true, MAP_JC),
+      GBFFT_TK(6, 64, false, true, MAP_JC),
       GBFFT_TK(7, 1, false, true, MAP_JC),
       GBFFT_TK(7, 2, false, true, MAP_JC),
       GBFFT_TK(7, 4, false, true, MAP_JC),
       GBFFT_TK(7, 8, false, true, MAP_JC),
       GBFFT_TK(7, 16, false, true, MAP_JC),
+      GBFFT_TK(7, 32, false, true, MAP_JC),
+      GBFFT_TK(7, 64, false, true, MAP_JC),
       GBFFT_TK(8, 1, false, true, MAP_JC),
       GBFFT_TK(8, 2, false, true, MAP_JC),
       GBFFT_TK(8, 4, false, true, MAP_JC),
       GBFFT_TK(8, 8, false, true, MAP_JC),
       GBFFT_TK(8, 16, false, true, MAP_JC),
+      GBFFT_TK(8, 32, false, true, MAP_JC),
+      GBFFT_TK(8, 64, false, true, MAP_JC),
   };
   for (const TileKernelInfo& k : tab)
     if (k.lg == lg && k.C == C) return &k;

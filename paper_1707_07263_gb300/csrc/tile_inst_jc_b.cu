@@ -10,6 +10,7 @@ const TileKernelInfo* tile_kernel_jc_b(int lg, int C) {
       GBFFT_TK(9, 4, false, true, MAP_JC),
       GBFFT_TK(9, 8, false, true, MAP_JC),
       GBFFT_TK(9, 16, false, true, MAP_JC),
+      GBFFT_TK(9, 32, false, true, MAP_JC),
       GBFFT_TK(10, 1, false, true, MAP_JC),
       GBFFT_TK(10, 2, false, true, MAP_JC),
       GBFFT_TK(10, 4, false, true, MAP_JC),

@@ -27,6 +27,12 @@ constexpr int jj_cols(int lg) { return lg >= 12 ? 1 : (lg >= 4 ? (4096 >> lg) : 
 const TileKernelInfo* tile_kernel_tma(int lg);
 constexpr int tma_exchange_width(int lg) { return lg >= 13 ? 4 : 8; }
 
+// Persistent tensor-TMA column kernels (tile_fft_tma2d.cuh), lengths 2^6..2^8.
+const TileKernelInfo* tile_kernel_coltma(int lg, int C);
+bool coltma_usable(const TileKernelInfo* k, const TileArgs& a, const void* in);
+int coltma_launch(const TileKernelInfo* k, const TileArgs& a, long long ntiles, int grid, int* status,
+                  cudaStream_t s);
+
 // Two-CTA radix-2 split kernels (tile_fft_dif2_kernel) for half length 2^lg.
 const TileKernelInfo* tile_kernel_dif2(int lg);
 

@@ -19,10 +19,10 @@ using namespace gbfft;
 
 static void add_cols(std::vector<fft_plan_config>& out, fft_plan_config base, int lg_a, int lg_b, int cols_a_max,
                      int cols_b_max) {
-  // columns per CTA: powers of two 2..16 keeping C * L <= 2^14 (compiled range)
-  for (int ca = 2; ca <= 16; ca *= 2) {
+  // columns per CTA: powers of two 2..64 keeping C * L <= 2^14 (compiled range)
+  for (int ca = 2; ca <= 64; ca *= 2) {
     if ((ca << lg_a) > (1 << 14) || ca > cols_a_max) continue;
-    for (int cb = 2; cb <= 16; cb *= 2) {
+    for (int cb = 2; cb <= 64; cb *= 2) {
       if ((cb << lg_b) > (1 << 14) || cb > cols_b_max) continue;
       fft_plan_config c = base;
       c.c1 = ca;
@@ -62,6 +62,8 @@ static std::vector<fft_plan_config> candidates(int lgN) {
       c.npass = 2;
       c.lg1 = lg1;
       add_cols(v, c, lg1, lg2, 1 << lg2, 1 << lg1);
+      c.tma = 1;  // default columns, tensor-TMA staged column pass
+      v.push_back(c);
     }
   }
   if (lgN >= 15) {
@@ -74,7 +76,20 @@ static std::vector<fft_plan_config> candidates(int lgN) {
         c.npass = 3;
         c.lg1 = l1;
         c.lg2 = l2;
+        v.push_back(c);  // default columns
+        c.tma = 1;       // ... with tensor-TMA staged column passes
         v.push_back(c);
+        c.tma = -1;
+        for (int ca = 16; ca <= 32; ca *= 2)
+          for (int cb = 16; cb <= 32; cb *= 2)
+            for (int cc = 8; cc <= 32; cc *= 2) {
+              if ((ca << l1) > (1 << 14) || (cb << l2) > (1 << 14) || (cc << l3) > (1 << 14)) continue;
+              fft_plan_config d = c;
+              d.c1 = ca;
+              d.c2 = cb;
+              d.c3 = cc;
+              v.push_back(d);
+            }
       }
   }
   return v;

@@ -204,13 +204,44 @@ def test_two_pass_forced_at_2_24(lib, monkeypatch):
 
 
 # --- full-size large transforms (config 3a) ----------------------------------------
-@pytest.mark.parametrize("lg", [24, 26])
-def test_fourstep_full_size(lib, lg):
+@pytest.mark.parametrize("lg,batch", [(24, 1), (26, 1), (24, 2)])
+def test_fourstep_full_size(lib, lg, batch):
     n = 1 << lg
-    x = workloads.uniform(n, 1, workloads.seed_for(2))
+    x = workloads.uniform(n, batch, workloads.seed_for(2))
     got = run_1d(lib, x, 0)
     ref = oracle.fft(x.astype(np.complex128))
     assert_rows(got, ref, tol32(n), f"N=2^{lg}")
+
+
+@pytest.mark.parametrize("lg", [27, 28])
+def test_maximum_lengths_by_properties(lib, lg):
+    """2^27 and 2^28 (the largest 1-D lengths) through properties that hold at
+    any size: a delta transforms to a constant, a single tone to one bin of
+    height N, Parseval, and the inverse round trip."""
+    n = 1 << lg
+    p = CPlan(lib, lib.fft_plan_create(n, 1, 0, 0))
+    x = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    x[5] = 1.0
+    X = p.run(x, 0)
+    k = torch.arange(n, device="cuda", dtype=torch.float64)
+    ph = torch.exp(-2j * torch.pi * torch.remainder(5 * k, n) / n)
+    assert float(torch.linalg.norm(X.to(torch.complex128) - ph) / np.sqrt(n)) <= tol32(n)
+    m = 12345
+    tone = torch.exp(2j * torch.pi * torch.remainder(m * k, n) / n).to(torch.complex64)
+    T = p.run(tone, 0).to(torch.complex128)
+    spike = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    spike[m] = n
+    assert float(torch.linalg.norm(T - spike) / n) <= tol32(n)
+    del tone, T, spike, ph
+    g = torch.Generator(device="cuda").manual_seed(lg)
+    r = torch.complex(torch.randn(n, device="cuda", generator=g), torch.randn(n, device="cuda", generator=g))
+    R = p.run(r, 0)
+    e_in = float(torch.sum(torch.abs(r.to(torch.complex128)) ** 2))
+    e_out = float(torch.sum(torch.abs(R.to(torch.complex128)) ** 2))
+    assert abs(e_out - n * e_in) <= 2 * tol32(n) * n * e_in
+    back = p.run(R, 1)
+    assert float(torch.linalg.norm((back - r).to(torch.complex128)) / torch.linalg.norm(r.to(torch.complex128))) \
+        <= 2 * tol32(n)
 
 
 # --- 2-D -----------------------------------------------------------------------
@@ -243,6 +274,17 @@ def test_2d_one_column_pass_forced(lib, monkeypatch):
     ref = oracle.fft2(x.astype(np.complex128))
     for b in range(2):
         assert oracle.rel_l2(got[b], ref[b]) <= tol32(4096 * 32)
+
+
+@pytest.mark.parametrize("ny,nx,batch", [(4096, 64, 2), (256, 512, 1), (2048, 16, 3)])
+def test_2d_tensor_tma_columns(lib, monkeypatch, ny, nx, batch):
+    """Column passes staged by tensor-TMA boxes (opt-in path)."""
+    monkeypatch.setenv("GBFFT_COLTMA", "1")
+    x = workloads.cgauss(ny * nx, batch, seed=ny + nx + 7).reshape(batch, ny, nx)
+    got = run_2d(lib, x, 1)
+    ref = oracle.fft2(x.astype(np.complex128), oracle.INVERSE)
+    for b in range(batch):
+        assert oracle.rel_l2(got[b], ref[b]) <= tol32(ny * nx)
 
 
 def test_2d_sar_full_size(lib):

@@ -49,6 +49,9 @@ def run_cfg(lib, x: np.ndarray, cfg: dict) -> np.ndarray:
     (20, {"npass": 2, "lg1": 9, "c1": 16, "c2": 8}),
     (20, {"npass": 3, "lg1": 7, "lg2": 7, "c1": 16, "c2": 8, "c3": 16}),
     (18, {"npass": 3, "lg1": 6, "lg2": 6}),
+    (16, {"npass": 2, "lg1": 8, "c1": 16, "c2": 8, "tma": 1}),
+    (20, {"npass": 2, "lg1": 8, "c1": 32, "c2": 4, "tma": 1}),
+    (21, {"npass": 3, "lg1": 7, "lg2": 7, "c1": 32, "c2": 16, "c3": 16, "tma": 1}),
     (12, {"npass": 1, "halves": 2}),
     (13, {"npass": 1, "halves": 2}),
     (14, {"npass": 1, "halves": 2}),
