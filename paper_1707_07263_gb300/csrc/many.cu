@@ -11,7 +11,8 @@
 //   kind 2  four-step row tile of such a transform, written transposed.
 // Queue order: every kind-1 tile (largest transforms first), then the batch
 // tiles (largest first), then every kind-2 tile.  CTAs pop items with one
-// atomicAdd on a queue head.  A kind-2 tile waits until all kind-1 tiles of
+// atomicAdd on a queue head, claiming the next item while working on the
+// current one.  A kind-2 tile waits until all kind-1 tiles of
 // its transform have been written (a per-transform completion counter); since
 // those were dequeued earlier by CTAs that never wait, the wait always ends --
 // it is still bounded (clock64 budget) and a timeout sets FFT_ERR_TIMEOUT in
@@ -178,13 +179,18 @@ __device__ __forceinline__ void many_row_tile(const ManyArgs& m, const ManyItem&
 
 __global__ void __launch_bounds__(kManyThreads, 3) many_kernel(const ManyArgs m) {
   extern __shared__ float2 smem[];
-  __shared__ int s_item;
+  __shared__ int s_next;
   __shared__ long long s_off[256];
-  while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(m.head, 1);
+  if (threadIdx.x == 0) s_next = atomicAdd(m.head, 1);
+  __syncthreads();
+  int idx = s_next;
+  while (idx < m.nitems) {
+    // claim the following item now (its index is read after this item's
+    // closing barrier); items are still claimed in queue order, and a CTA's
+    // claimed-but-unstarted item starts as soon as its current one ends, so
+    // the earliest unfinished item is always being worked on
     __syncthreads();
-    const int idx = s_item;
-    if (idx >= m.nitems) return;
+    if (threadIdx.x == 0) s_next = atomicAdd(m.head, 1);
     const ManyItem it = m.items[idx];
     TileArgs a;
     memset(&a, 0, sizeof(a));
@@ -225,7 +231,8 @@ __global__ void __launch_bounds__(kManyThreads, 3) many_kernel(const ManyArgs m)
       else if (t.lg2 == 7) many_row_tile<7>(m, it, t, a, smem);
       else many_row_tile<8>(m, it, t, a, smem);
     }
-    __syncthreads();  // smem and s_item are reused by the next item
+    __syncthreads();  // smem is reused by the next item; s_next is published
+    idx = s_next;
   }
 }
 
