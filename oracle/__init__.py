@@ -15,6 +15,11 @@ Functions (all FP64, numpy ``complex128`` in and out):
 * ``fft2(x, dir)``      -- 2-D transform of the last two axes, rows then
                            columns (Sec. 2.3.2 treats the data as 2-D/3-D and
                            transforms each dimension in turn).
+* ``range_compress(x, H)`` -- SAR range compression by fast convolution, the
+  FFT-based SAR processing that Sec. 3 and Sec. 4 name as the method's
+  application: every row becomes Eq. 2 applied to H * (Eq. 1 applied to the
+  row), i.e. the circular convolution of the row with the inverse transform
+  of H (for a matched filter H, the correlation with the transmitted pulse).
 * ``spectral_loss(x, w)`` and ``spectral_loss_grad(x, w)`` -- the loss
   L = sum_k |w_k X_k|^2 with X = Eq. 1 applied to x, and its gradient in
   PyTorch's convention (dL/dRe + i dL/dIm) = 2 F^H (w^2 * F x), where F^H is
@@ -132,6 +137,17 @@ def transform(x, dir: int = FORWARD, lib=None) -> np.ndarray:
     recursion above that."""
     n = np.asarray(x).shape[-1]
     return dft(x, dir, lib) if n <= 1024 else fft(x, dir, lib)
+
+
+def range_compress(x, H, lib=None) -> np.ndarray:
+    """Rows of x (last axis, length n) each become IDFT(H * DFT(row)): Eq. 1,
+    the pointwise product with the n-point frequency-domain filter H (shared
+    by every row, natural frequency order), then Eq. 2 with its 1/n."""
+    x = np.asarray(x, dtype=np.complex128)
+    H = np.asarray(H, dtype=np.complex128)
+    if H.shape != x.shape[-1:]:
+        raise ValueError(f"range_compress: filter of shape {H.shape} for rows of length {x.shape[-1]}")
+    return transform(transform(x, FORWARD, lib) * H, INVERSE, lib)
 
 
 def spectral_loss(x, w) -> float:

@@ -15,6 +15,11 @@ Distributions:
 * ``sar_image`` -- unit CN(0,1) speckle plus point scatterers of amplitude A
                    and uniform random phase at distinct random pixels.
 * ``uneven_lengths`` -- lengths 2^e with e uniform over the integers lo..hi.
+* ``lfm_pulse`` / ``range_lines`` / ``range_filter`` -- SAR range lines: a
+  linear-FM (chirp) pulse, echoes of it from point targets at random delays
+  in CN(0,1) receiver noise, and the frequency-domain matched filter written
+  in closed form by the principle of stationary phase (no transform is
+  computed here).
 """
 from __future__ import annotations
 
@@ -84,3 +89,45 @@ def real_weights(n: int, seed: int = SEED_BASE) -> np.ndarray:
     """float32 weights ~ U[0, 1] (the spectral-loss weights w)."""
     g = _rng(seed)
     return g.uniform(0.0, 1.0, size=n).astype(np.float32)
+
+
+def lfm_pulse(n: int, n_pulse: int, bw: float = 0.8) -> np.ndarray:
+    """complex64 (n,): a unit-amplitude linear-FM pulse of n_pulse samples,
+    s[t] = exp(i pi K (t - n_pulse/2)^2) for t < n_pulse and 0 after, swept
+    over bw cycles per sample (chirp rate K = bw / n_pulse)."""
+    t = np.arange(n, dtype=np.float64)
+    K = bw / n_pulse
+    s = np.exp(1j * np.pi * K * (t - n_pulse / 2.0) ** 2)
+    s[n_pulse:] = 0.0
+    return s.astype(np.complex64)
+
+
+def range_lines(n: int, batch: int, n_pulse: int, n_targets: int = 8, bw: float = 0.8,
+                noise: float = 1.0, seed: int = SEED_BASE) -> np.ndarray:
+    """complex64 (batch, n) raw range lines: per line, n_targets echoes of
+    lfm_pulse (amplitudes U[1, 10], phases U[0, 2 pi), circular delays
+    uniform over 0..n-1) plus CN(0, noise^2) receiver noise."""
+    g = _rng(seed)
+    s = lfm_pulse(n, n_pulse, bw).astype(np.complex128)
+    sc = np.sqrt(0.5) * noise
+    out = g.normal(0.0, sc, size=(batch, n)) + 1j * g.normal(0.0, sc, size=(batch, n))
+    amp = g.uniform(1.0, 10.0, size=(batch, n_targets))
+    ph = g.uniform(0.0, 2.0 * np.pi, size=(batch, n_targets))
+    dl = g.integers(0, n, size=(batch, n_targets))
+    for b in range(batch):
+        for t in range(n_targets):
+            out[b] += amp[b, t] * np.exp(1j * ph[b, t]) * np.roll(s, dl[b, t])
+    return out.astype(np.complex64)
+
+
+def range_filter(n: int, n_pulse: int, bw: float = 0.8) -> np.ndarray:
+    """complex64 (n,): the matched filter of lfm_pulse in the frequency domain
+    by stationary phase, H(f) = exp(i pi f^2 / K) exp(2 pi i f n_pulse / 2)
+    for |f| <= bw/2 (zero outside), f = k/n for k < n/2 and k/n - 1 above
+    (cycles per sample), K = bw / n_pulse."""
+    k = np.arange(n, dtype=np.float64)
+    f = np.where(k < n / 2, k / n, k / n - 1.0)
+    K = bw / n_pulse
+    H = np.exp(1j * np.pi * f * f / K) * np.exp(2j * np.pi * f * (n_pulse / 2.0))
+    H[np.abs(f) > bw / 2.0] = 0.0
+    return H.astype(np.complex64)

@@ -183,5 +183,41 @@ def check_fft2(lib, shapes=((4, 8), (32, 16), (64, 128))):
         _close(oracle.fft2(d, lib=lib), ref, 1e-13, f"fft2 delta {ny}x{nx}")
 
 
+def check_range_compress(lib, rc=None):
+    """Range compression (fast convolution) against definitions that do not
+    go through a transform: the circular-convolution sum, the shift theorem,
+    the identity filter and the matched-filter peak of a linear-FM pulse."""
+    if rc is None:
+        def rc(x, H):
+            return oracle.range_compress(x, H, lib=lib)
+    # (a) brute force: H = sum_t h[t] e^{-2 pi i k t / n} written out here;
+    #     y[m] = sum_t x[t] h[(m - t) mod n]
+    for n in (1, 2, 4, 8, 16, 32):
+        x = _cvec(n, seed=500 + n, batch=3)
+        h = _cvec(n, seed=600 + n)
+        t = np.arange(n)
+        H = np.array([np.sum(h * np.exp(-2j * np.pi * ((k * t) % n) / n)) for k in range(n)])
+        ref = np.array([[np.sum(row * h[(m - t) % n]) for m in range(n)] for row in x])
+        _close(rc(x, H), ref, 1e-12, f"range compression = circular convolution, n={n}")
+    # (b) shift theorem: H[k] = W_n^{k d} delays every row by d samples
+    for n, d in ((64, 5), (2048, 1000), (4096, 4095)):
+        x = _cvec(n, seed=700 + n, batch=2)
+        k = np.arange(n)
+        H = np.exp(-2j * np.pi * ((k * d) % n) / n)
+        _close(rc(x, H), np.roll(x, d, axis=-1), 1e-12, f"range compression shift n={n} d={d}")
+    # (c) identity filter
+    x = _cvec(512, seed=801, batch=2)
+    _close(rc(x, np.ones(512)), x, 1e-13, "range compression identity")
+    # (d) matched filter of a unit-amplitude LFM pulse of P samples: the echo
+    #     delayed by d compresses to a peak of height P (the pulse energy) at d
+    n, P, d = 1024, 200, 333
+    t = np.arange(n)
+    s = np.where(t < P, np.exp(1j * np.pi * (0.8 / P) * (t - P / 2) ** 2), 0)
+    y = rc(np.roll(s, d)[None, :], np.conj(np.fft.fft(s)))[0]
+    assert int(np.argmax(np.abs(y))) == d, "matched-filter peak position"
+    assert abs(y[d] - P) <= 1e-9 * P, f"matched-filter peak height {y[d]} != {P}"
+    assert np.max(np.abs(np.delete(y, d))) < 0.5 * P, "matched-filter sidelobes"
+
+
 ALL_CHECKS = (check_golden, check_small_by_hand, check_closed_forms, check_invariants,
-              check_dft_vs_fft, check_numpy, check_fft2)
+              check_dft_vs_fft, check_numpy, check_fft2, check_range_compress)

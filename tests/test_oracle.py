@@ -112,3 +112,40 @@ def test_pins_catch_mutation(name):
             except (AssertionError, ValueError):
                 failures += 1
         assert failures > 0, f"no pin caught mutation {name}"
+
+
+# Plausible mistakes in composing the range compression (planted in a copy of
+# the function, on the CPU); its pin must fail for each.
+RC_MUTATIONS = {
+    "filter_conjugated": lambda x, H: oracle.transform(oracle.transform(x) * np.conj(H), oracle.INVERSE),
+    "adjoint_not_inverse": lambda x, H: oracle.transform(oracle.transform(x) * H, oracle.ADJOINT),
+    "forward_twice": lambda x, H: oracle.transform(oracle.transform(x) * H, oracle.FORWARD),
+    "filter_reversed": lambda x, H: oracle.transform(oracle.transform(x) * np.asarray(H)[::-1], oracle.INVERSE),
+    "filter_on_input": lambda x, H: oracle.transform(oracle.transform(np.asarray(x) * H), oracle.INVERSE),
+}
+
+
+@pytest.mark.parametrize("name", sorted(RC_MUTATIONS))
+def test_range_pin_catches_mutation(lib, name):
+    with pytest.raises(AssertionError):
+        pins.check_range_compress(lib, rc=RC_MUTATIONS[name])
+
+
+def test_range_compress_rejects_bad_filter():
+    with pytest.raises(ValueError):
+        oracle.range_compress(np.ones((2, 8)), np.ones(4))
+
+
+def test_range_workload_compresses():
+    """The synthetic SAR lines and the closed-form matched filter fit each
+    other: one noiseless echo per line compresses to a sharp peak at its
+    delay (the generator draws noise, amplitudes, phases, then delays)."""
+    from paper_1707_07263_gb300 import workloads
+    n, P, seed = 4096, 1000, 5
+    x = workloads.range_lines(n, 4, P, n_targets=1, noise=0.0, seed=seed)
+    y = np.abs(oracle.range_compress(x, workloads.range_filter(n, P)))
+    g = np.random.Generator(np.random.PCG64(seed))
+    g.normal(size=(4, n)), g.normal(size=(4, n)), g.uniform(size=(4, 1)), g.uniform(size=(4, 1))
+    delays = g.integers(0, n, size=(4, 1)).ravel()
+    assert np.array_equal(np.argmax(y, axis=1), delays)
+    assert np.all(y.max(axis=1) > 1000 * np.median(y, axis=1))
