@@ -101,6 +101,20 @@ GBFFT_API int fft_exec(fft_plan* plan, const void* in, void* out, void* stream);
  * tables serve every direction); used for the adjoint in backpropagation. */
 GBFFT_API int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* stream);
 
+/* Whether the GPU can read and write the `bytes` bytes at `ptr` through that
+ * same address, so that fft_exec may take it as `in` or `out`: memory of the
+ * current device, managed memory, or page-locked host memory mapped into the
+ * device's address space at the same address (cudaHostAlloc or
+ * cudaHostRegister under unified addressing, the default on 64-bit hosts).
+ * Both ends of the range are checked.  Returns 1 if usable, 0 if not
+ * (pageable or unknown host memory, another device's memory, a mapping at a
+ * different device address), or a negative error code (FFT_ERR_INVALID_ARG
+ * for NULL or bytes == 0).  With mapped host memory the kernels read and
+ * write the batch over the host link while they transform it, with no
+ * separate copy and no device buffer (the host<->device transfer that Sec. 3
+ * and Sec. 4 count in their GPU times). */
+GBFFT_API int fft_pointer_usable(const void* ptr, size_t bytes);
+
 /* Explicit plan configuration (npass, lg1, lg2, c1, c2, c3 <= 0 mean
  * "planner default"; tma, fused < 0 mean default).  npass: 1 = one on-chip
  * pass (n <= 2^14), 2 = two passes N = 2^lg1 * 2^(lgN-lg1), 3 = three passes

@@ -14,7 +14,8 @@ from ._lib import (FFT_ADJOINT, FFT_FORWARD, FFT_INVERSE, FFT_PREC_FP32, FFT_PRE
 
 def __getattr__(name):
     # lazy: torch and the CUDA library are only touched when the API is used
-    if name in ("fft", "ifft", "fft2", "ifft2", "fft_many", "Plan", "get_plan", "clear_plan_cache", "PREC"):
+    if name in ("fft", "ifft", "fft2", "ifft2", "fft_many", "fft_host", "HostPipeline", "Plan", "get_plan",
+                "clear_plan_cache", "PREC"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -66,6 +66,7 @@ SIGNATURES = {
     "fft_plan_get_config": (_int, [_vp, ctypes.POINTER(FftPlanConfig)]),
     "fft_autotune": (_int, [_i64, _i64, _int, _vp, _vp, _vp, _sz, _vp, _int, ctypes.POINTER(FftPlanConfig),
                             ctypes.POINTER(ctypes.c_float)]),
+    "fft_pointer_usable": (_int, [_vp, _sz]),
     "fft_last_error": (_int, []),
     "fft_error_string": (ctypes.c_char_p, [_int]),
 }

@@ -229,3 +229,145 @@ def fft_many(packed: torch.Tensor, lengths, inverse: bool = False, prec="fp32") 
     if packed.numel() != sum(lengths):
         raise ValueError("packed size does not match the sum of the lengths")
     return _FFTMany.apply(packed.reshape(-1), lengths, INVERSE if inverse else FORWARD, prec)
+
+
+class HostPipeline:
+    """Transforms of data that lives in (pinned) HOST memory, end to end.
+
+    The paper's GPU times include moving the data to and from the device, the
+    part it finds limiting (Sec. 3, Sec. 4).  Two ways across the host link:
+
+    direct  the plan runs on the host buffers themselves: its kernels read the
+            input and write the output over the link (page-locked memory that
+            the library reports usable, fft_pointer_usable).  One launch per
+            pass, no device buffer for the data and no copy engine.
+    copy    the batch is cut into chunks and three CUDA streams overlap the
+            upload of chunk i+1, the transform of chunk i and the download of
+            chunk i-1, events ordering each chunk's steps; two device buffers
+            per stage, allocated on first use.
+
+    direct=None picks direct for one-pass plans when both buffers are usable
+    and copy otherwise; True / False force one (True raises if a buffer is not
+    usable).  n: transform length; batch: transforms per call; chunk:
+    transforms per chunk of the copy mode (default: about 64 MiB); streams: an
+    optional (upload, transform, download) stream triple shared by several
+    pipelines so that they overlap one another.
+    """
+
+    def __init__(self, n: int, batch: int, dir: int = FORWARD, prec="fp32", device=None, chunk: int | None = None,
+                 streams=None, direct: bool | None = None):
+        self.n, self.batch, self.dir, self.prec = int(n), int(batch), int(dir), prec
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.lib = L.load()
+        if chunk is None:
+            chunk = max(1, (64 << 20) // (8 * self.n))
+        self.chunk = int(min(max(1, chunk), self.batch))
+        self.nchunks = (self.batch + self.chunk - 1) // self.chunk
+        self.want_direct = direct
+        self.full_plan = None
+        if direct is not False:
+            self.full_plan = get_plan("1d", (self.n,), self.batch, prec, self.device)
+            if direct is None and self.full_plan.launches != 1:
+                self.full_plan = None
+        self.plan = self.tail_plan = None
+        self.dev_in = self.dev_out = None
+        if streams is None:
+            streams = tuple(torch.cuda.Stream(self.device) for _ in range(3))
+        self.streams = tuple(streams)
+        self.s_h2d, self.s_fft, self.s_d2h = self.streams
+        self.last_mode = None
+
+    def usable(self, t: torch.Tensor) -> bool:
+        """True if the library's kernels can address t's storage directly."""
+        with torch.cuda.device(self.device):
+            rc = int(self.lib.fft_pointer_usable(ctypes.c_void_p(t.data_ptr()), t.numel() * t.element_size()))
+        if rc < 0:
+            raise L.GbfftError(rc, "fft_pointer_usable")
+        return rc == 1
+
+    def _copy_setup(self):
+        if self.plan is not None:
+            return
+        self.plan = get_plan("1d", (self.n,), self.chunk, self.prec, self.device)
+        tail = self.batch - (self.nchunks - 1) * self.chunk
+        if tail != self.chunk:
+            self.tail_plan = get_plan("1d", (self.n,), tail, self.prec, self.device)
+        el = self.chunk * self.n
+        self.dev_in = [torch.empty(el, dtype=torch.complex64, device=self.device) for _ in range(2)]
+        self.dev_out = [torch.empty(el, dtype=torch.complex64, device=self.device) for _ in range(2)]
+
+    def __call__(self, x_host: torch.Tensor, out_host: torch.Tensor, join: bool = True) -> torch.Tensor:
+        """x_host, out_host: contiguous complex64 host tensors of batch*n
+        elements (pin them for asynchronous copies or the direct mode).
+        Returns out_host once the work is queued; synchronise the current
+        stream before reading it.  join=False leaves the current stream
+        unordered after the last step (the caller joins the download stream
+        itself, e.g. after the last of several pipelines on shared streams)."""
+        if x_host.is_cuda or out_host.is_cuda:
+            raise TypeError("HostPipeline takes host tensors")
+        if x_host.dtype != torch.complex64 or out_host.dtype != torch.complex64:
+            raise TypeError("expected complex64 tensors")
+        if x_host.numel() != self.batch * self.n or out_host.numel() != self.batch * self.n:
+            raise ValueError("expected batch*n elements")
+        xf, of = x_host.reshape(-1), out_host.reshape(-1)
+        cur = torch.cuda.current_stream(self.device)
+        direct = self.full_plan is not None and self.usable(xf) and self.usable(of)
+        if self.want_direct and not direct:
+            raise ValueError("direct mode needs page-locked host buffers the GPU can address")
+        for s in self.streams:
+            s.wait_stream(cur)
+        if direct:
+            self.last_mode = "direct"
+            self.full_plan.exec_ptr(xf.data_ptr(), of.data_ptr(), self.dir, self.s_fft)
+            self.s_d2h.wait_stream(self.s_fft)
+            self.s_h2d.wait_stream(self.s_fft)
+            if join:
+                cur.wait_stream(self.s_d2h)
+            return out_host
+        self.last_mode = "copy"
+        self._copy_setup()
+        uploaded = [None, None]
+        transformed = [None, None]
+        downloaded = [None, None]
+        for i in range(self.nchunks):
+            b = i % 2
+            lo = i * self.chunk * self.n
+            m = min(self.chunk, self.batch - i * self.chunk) * self.n
+            plan = self.plan if m == self.chunk * self.n else self.tail_plan
+            with torch.cuda.stream(self.s_h2d):
+                if transformed[b] is not None:
+                    self.s_h2d.wait_event(transformed[b])      # dev_in[b] free again
+                self.dev_in[b][:m].copy_(xf[lo:lo + m], non_blocking=True)
+                uploaded[b] = torch.cuda.Event()
+                uploaded[b].record(self.s_h2d)
+            with torch.cuda.stream(self.s_fft):
+                self.s_fft.wait_event(uploaded[b])
+                if downloaded[b] is not None:
+                    self.s_fft.wait_event(downloaded[b])       # dev_out[b] free again
+                plan.exec_ptr(self.dev_in[b].data_ptr(), self.dev_out[b].data_ptr(), self.dir, self.s_fft)
+                transformed[b] = torch.cuda.Event()
+                transformed[b].record(self.s_fft)
+            with torch.cuda.stream(self.s_d2h):
+                self.s_d2h.wait_event(transformed[b])
+                of[lo:lo + m].copy_(self.dev_out[b][:m], non_blocking=True)
+                downloaded[b] = torch.cuda.Event()
+                downloaded[b].record(self.s_d2h)
+        if join:
+            cur.wait_stream(self.s_d2h)
+        return out_host
+
+
+def fft_host(x_host: torch.Tensor, out_host: torch.Tensor | None = None, inverse: bool = False,
+             chunk: int | None = None, direct: bool | None = None) -> torch.Tensor:
+    """Eq. 1 (or Eq. 2) over the last dimension of a HOST complex64 tensor,
+    through a HostPipeline (direct on page-locked buffers for one-pass plans,
+    else pipelined copies).  Synchronous: returns when the result is in
+    out_host."""
+    n = x_host.shape[-1]
+    batch = x_host.numel() // n
+    if out_host is None:
+        out_host = torch.empty(x_host.shape, dtype=x_host.dtype, pin_memory=torch.cuda.is_available())
+    pipe = HostPipeline(n, batch, INVERSE if inverse else FORWARD, chunk=chunk, direct=direct)
+    pipe(x_host.contiguous(), out_host)
+    torch.cuda.synchronize(pipe.device)
+    return out_host
