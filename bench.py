@@ -23,7 +23,7 @@ Also printed on the same JSON line:
 
 ``--impl reference`` times the oracle instead (the deliberately slow CPU
 baseline) and prints the same line with "impl": "reference".
-Other workloads for measurement only: --workload large | 2d | tc | many | cfg1.
+Other workloads for measurement only: --workload large | tc | many | range.
 """
 from __future__ import annotations
 
@@ -679,6 +679,56 @@ def run_measure(args):
                     "grad_rel_l2_max_sampled": float(f"{max(errs):.3e}"), "grad_samples": len(errs)})
         desc = ("uneven batch: 4096 transforms, lengths 2^e with e uniform over 8..16, CN(0,1); "
                 "graph-captured forward + loss gradient + adjoint backward")
+    elif args.workload == "range":
+        # SAR range compression: 2^26 / N range lines of N samples, each the
+        # echoes of a linear-FM pulse of N/4 samples; closed-form matched filter
+        for lg in (12, 13, 14, 16, 20):
+            n = 1 << lg
+            batch = TOTAL // n
+            P = n // 4
+            xh = workloads.range_lines(n, batch, P, n_targets=2, seed=workloads.seed_for(6) + lg)
+            Hh = workloads.range_filter(n, P)
+            x = torch.from_numpy(xh.reshape(-1)).to(dev)
+            H = torch.from_numpy(Hh).to(dev)
+            y = torch.empty_like(x)
+            X = torch.empty_like(x)
+            p = api.Plan("1d", (n,), batch, device=dev)
+            fused = _time_fn(torch, lambda: p.exec_filter_ptr(x.data_ptr(), y.data_ptr(), H.data_ptr(), stream),
+                             args.steps, args.warmup, stream)
+            X2 = X.view(batch, n)
+
+            def unfused():
+                p.exec_ptr(x.data_ptr(), X.data_ptr(), 0, stream)
+                with torch.cuda.stream(stream):
+                    torch.mul(X2, H, out=X2)
+                p.exec_ptr(X.data_ptr(), y.data_ptr(), 1, stream)
+
+            sep = _time_fn(torch, unfused, args.steps, args.warmup, stream)
+
+            def cufft():
+                with torch.cuda.stream(stream):
+                    torch.fft.ifft(torch.fft.fft(x.view(batch, n)) * H)
+
+            cu = _time_fn(torch, cufft, args.steps, args.warmup, stream)
+            p.exec_filter_ptr(x.data_ptr(), y.data_ptr(), H.data_ptr(), stream)
+            torch.cuda.synchronize()
+            rows = [0, batch // 2, batch - 1]
+            ref = oracle.range_compress(xh[rows].astype(np.complex128), Hh.astype(np.complex128))
+            got = y.view(batch, n)[rows].cpu().numpy().astype(np.complex128)
+            scale = np.abs(Hh).max() * np.sqrt(np.sum(np.abs(xh[rows].astype(np.complex128)) ** 2, axis=-1))
+            err = float(np.max(np.sqrt(np.sum(np.abs(got - ref) ** 2, axis=-1)) / scale))
+            fl = (10.0 * n * lg + 6.0 * n) * batch
+            nl = p.launches
+            res.append({"n": n, "lines": batch, "pulse": P, "fused_us": round(fused * 1e3, 1),
+                        "unfused_us": round(sep * 1e3, 1), "cufft_torch_us": round(cu * 1e3, 1),
+                        "gflops": round(fl / (fused * 1e-3) / 1e9, 1),
+                        "hbm_frac_algorithmic": round(16.0 * n * batch / (fused * 1e-3) / 1e9 / peak, 4),
+                        "launches": 1 if nl == 1 else 2 * nl,
+                        "err_sampled": float(f"{err:.3e}")})
+            del p
+        desc = ("SAR range compression IFFT(H * FFT(line)): 2^26/N lines of N samples, LFM echoes + CN(0,1) "
+                "noise, closed-form matched filter; fused = fft_exec_filter, unfused = FFT, torch multiply, "
+                "IFFT; cufft_torch = torch.fft (context)")
     print(json.dumps({"workload": args.workload, "desc": desc, "results": res,
                       "peak_hbm_gbs": peak}), flush=True)
 
@@ -689,7 +739,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

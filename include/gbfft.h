@@ -101,6 +101,27 @@ GBFFT_API int fft_exec(fft_plan* plan, const void* in, void* out, void* stream);
  * tables serve every direction); used for the adjoint in backpropagation. */
 GBFFT_API int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* stream);
 
+/* SAR range compression (fast convolution; Sec. 3 and Sec. 4 name FFT-based
+ * SAR processing as the method's application): each of the plan's `batch`
+ * rows x_b of length n becomes
+ *     y_b = IFFT( H .* FFT(x_b) )      (Eq. 1, pointwise product, Eq. 2)
+ * with one n-point frequency-domain filter H for every row (for a matched
+ * filter, the conjugated spectrum of the transmitted pulse).
+ *   plan:  a 1-D FP32 plan of fft_plan_create / fft_plan_create_config (not a
+ *          fused two-pass configuration); its direction is not used.
+ *   in, out: batch*n complex64 values, 8-byte aligned, device memory or memory
+ *          fft_pointer_usable accepts; in == out allowed.
+ *   filt:  n complex64 values in natural frequency order (k < n/2: k/n cycles
+ *          per sample; k >= n/2: k/n - 1), 8-byte aligned, same kinds of memory.
+ * n <= 2^14: one fused kernel; each row is read once and written once, the
+ * product and both transforms on chip (separate calls move every value through
+ * memory three times).  Longer n: the plan's passes run twice, the product
+ * fused into the last pass of the first run; `out` holds the intermediate and
+ * the plan's workspace is used.  Asynchronous on `stream`, no allocation,
+ * capturable.  FFT_ERR_UNSUPPORTED for 2-D, uneven-batch, tensor-core and
+ * fused two-pass plans. */
+GBFFT_API int fft_exec_filter(fft_plan* plan, const void* in, void* out, const void* filt, void* stream);
+
 /* Whether the GPU can read and write the `bytes` bytes at `ptr` through that
  * same address, so that fft_exec may take it as `in` or `out`: memory of the
  * current device, managed memory, or page-locked host memory mapped into the

@@ -67,6 +67,7 @@ SIGNATURES = {
     "fft_autotune": (_int, [_i64, _i64, _int, _vp, _vp, _vp, _sz, _vp, _int, ctypes.POINTER(FftPlanConfig),
                             ctypes.POINTER(ctypes.c_float)]),
     "fft_pointer_usable": (_int, [_vp, _sz]),
+    "fft_exec_filter": (_int, [_vp, _vp, _vp, _vp, _vp]),
     "fft_last_error": (_int, []),
     "fft_error_string": (ctypes.c_char_p, [_int]),
 }

@@ -104,6 +104,12 @@ class Plan:
         self.exec_ptr(x.data_ptr(), out.data_ptr(), dir, stream)
         return out
 
+    def exec_filter_ptr(self, in_ptr: int, out_ptr: int, filt_ptr: int, stream=None) -> None:
+        """Range compression IFFT(H * FFT(row)) of every row (fft_exec_filter)."""
+        rc = self.lib.fft_exec_filter(self.handle, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+                                      ctypes.c_void_p(filt_ptr), ctypes.c_void_p(_stream_handle(stream)))
+        L.check(rc, "fft_exec_filter")
+
     def status(self, stream=None) -> int:
         return int(self.lib.fft_status(self.handle, ctypes.c_void_p(_stream_handle(stream))))
 
@@ -229,6 +235,47 @@ def fft_many(packed: torch.Tensor, lengths, inverse: bool = False, prec="fp32") 
     if packed.numel() != sum(lengths):
         raise ValueError("packed size does not match the sum of the lengths")
     return _FFTMany.apply(packed.reshape(-1), lengths, INVERSE if inverse else FORWARD, prec)
+
+
+def _run_filter(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
+    n = x.shape[-1]
+    batch = x.numel() // n if n else 0
+    out = torch.empty_like(x)
+    if batch == 0:
+        return out
+    p = get_plan("1d", (n,), batch, "fp32", x.device)
+    p.exec_filter_ptr(x.data_ptr(), out.data_ptr(), H.data_ptr())
+    return out
+
+
+class _RangeCompress(torch.autograd.Function):
+    """y = F^{-1} diag(H) F x per row.  Its adjoint is F^{-1} diag(conj H) F,
+    so the backward pass is the same fused operation with the conjugated
+    filter (no gradient for H)."""
+
+    @staticmethod
+    def forward(ctx, x, H):
+        ctx.save_for_backward(H)
+        return _run_filter(x, H)
+
+    @staticmethod
+    def backward(ctx, g):
+        (H,) = ctx.saved_tensors
+        return _run_filter(g.contiguous(), H.conj().resolve_conj().contiguous()), None
+
+
+def range_compress(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
+    """SAR range compression (fast convolution) over the last dimension:
+    IFFT(H * FFT(row)) for every row, with one fused kernel per tile for
+    rows of up to 2^14 points (Eq. 1, pointwise product, Eq. 2).  x: complex64
+    CUDA tensor (..., n); H: complex64 CUDA tensor of n filter values in
+    natural frequency order.  Differentiable in x."""
+    _check_input(x)
+    if H.dtype != torch.complex64 or not H.is_cuda or H.shape != x.shape[-1:]:
+        raise TypeError("H must be a complex64 CUDA tensor of shape (n,)")
+    if H.device != x.device:
+        raise ValueError("x and H must be on the same device")
+    return _RangeCompress.apply(x.contiguous(), H.detach().contiguous())
 
 
 class HostPipeline:

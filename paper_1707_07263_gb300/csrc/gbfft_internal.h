@@ -51,6 +51,7 @@ struct fft_plan {
   const gbfft::TileKernelInfo* k2;
   const gbfft::TileKernelInfo* ktma;  // persistent TMA-staged single-pass kernel (or NULL)
   const gbfft::TileKernelInfo* kdif2; // two-CTA radix-2 split kernel (or NULL)
+  const gbfft::TileKernelInfo* krc;   // fused range-compression kernel of the length (or NULL)
   const float2* pre_tw;               // its W_N^n table, n < N/2
   long long tma_grid;                 // its resident-CTA grid
 

@@ -313,6 +313,69 @@ static int exec_passes(fft_plan* p, const float2* in, float2* out, int dir, cuda
   return FFT_OK;
 }
 
+// ---- range compression (fast convolution with a frequency-domain filter) --
+// One-pass lengths: the fused kernel, one read and one write per value.
+// Multi-pass plans: the passes run twice.  The first run is the forward
+// transform whose last (row) pass stores conj(H X); the second is a forward
+// transform of that, conjugated and scaled by 1/N on its last store, which is
+// Eq. 2 applied to H X.  `out` holds the intermediate.
+static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const float2* filt, cudaStream_t s) {
+  if (p->prec != FFT_PREC_FP32) return FFT_ERR_UNSUPPORTED;
+  const float inv_n = (float)(1.0 / (double)p->n);
+  if (p->kind == KIND_SINGLE) {
+    if (!p->krc) return FFT_ERR_UNSUPPORTED;
+    TileArgs a;
+    base_args(a);
+    const int C = p->krc->C;
+    const long long L = p->n;
+    a.in = in;
+    a.out = out;
+    a.tw = p->tw1;
+    a.tiles_per_batch = (p->batch + C - 1) / C;
+    a.in_gstride = a.out_gstride = (long long)C * L;
+    a.in_sc = a.out_sc = L;
+    a.in_sn = a.out_sn = 1;
+    a.ncols = p->batch;
+    a.filt = filt;
+    a.filt_mask = L - 1;
+    a.scale_out = 1;
+    a.sx = inv_n;
+    a.sy = -inv_n;
+    return launch_tile(p->krc, a, a.tiles_per_batch, s);
+  }
+  if (p->kind != KIND_FOURSTEP || p->fused || p->npass < 2) return FFT_ERR_UNSUPPORTED;
+  if (p->pass[p->npass - 1].k->map != MAP_JC) return FFT_ERR_UNSUPPORTED;
+  float2* roles[3] = {(float2*)in, out, (float2*)p->ws};
+  for (int run = 0; run < 2; ++run) {
+    if (run == 1) roles[0] = out;
+    for (int i = 0; i < p->npass; ++i) {
+      const PassDesc& d = p->pass[i];
+      if ((d.in_role == 2 || d.out_role == 2) && !p->ws) return FFT_ERR_NO_WORKSPACE;
+      TileArgs a = d.a;
+      a.in = roles[d.in_role];
+      a.out = roles[d.out_role];
+      if (i == 0) a.conj_in = 0;
+      if (i == p->npass - 1) {
+        a.scale_out = 1;
+        if (run == 0) {
+          a.filt = filt;
+          a.filt_mask = p->n - 1;
+          a.sx = 1.0f;
+          a.sy = -1.0f;
+        } else {
+          a.sx = inv_n;
+          a.sy = -inv_n;
+        }
+      }
+      const int rc = (d.kcol && coltma_usable(d.kcol, a, a.in))
+                         ? coltma_launch(d.kcol, a, d.ntiles, d.col_grid, p->d_status, s)
+                         : launch_tile(d.k, a, d.ntiles, s);
+      if (rc) return rc;
+    }
+  }
+  return FFT_OK;
+}
+
 int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
   if (!p || !in || !out || !valid_dir(dir)) return FFT_ERR_INVALID_ARG;
   if (((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return FFT_ERR_ALIGN;
@@ -382,6 +445,11 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     p->launches = 1;
     int rc = prepare_kernel(p->k1);
     if (rc) return rc;
+    if (p->prec == FFT_PREC_FP32) {
+      p->krc = tile_kernel_rc(lgN);
+      rc = prepare_kernel(p->krc);
+      if (rc) return rc;
+    }
     // Two CTAs per transform (radix-2 split) is an autotuner option: with the
     // linear shared-memory addressing the one-CTA pass measures faster at
     // 2^12..2^14 on GB300.  Persistent TMA staging pays where several CTAs
@@ -867,6 +935,17 @@ int fft_exec(fft_plan* plan, const void* in, void* out, void* stream) {
 
 int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* stream) {
   return set_err(exec_plan(plan, in, out, dir, (cudaStream_t)stream));
+}
+
+int fft_exec_filter(fft_plan* plan, const void* in, void* out, const void* filt, void* stream) {
+  if (!plan || !in || !out || !filt) return set_err(FFT_ERR_INVALID_ARG);
+  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7) || ((uintptr_t)filt & 7)) return set_err(FFT_ERR_ALIGN);
+  int rc = exec_filter_plan(plan, (const float2*)in, (float2*)out, (const float2*)filt, (cudaStream_t)stream);
+  if (rc == FFT_OK && cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    rc = FFT_ERR_CUDA;
+  }
+  return set_err(rc);
 }
 
 void fft_destroy(fft_plan* plan) { free_plan(plan); }

@@ -160,6 +160,14 @@ struct TileArgs {
   // with W_{2 pre_half}^n read from pre_tw; k1 arrives as the pass's bidx.
   long long pre_half;
   const float2* pre_tw;
+  // Frequency-domain filter of range compression (Sec. 3, Sec. 4: FFT-based
+  // SAR processing), complex64 in natural frequency order.  Fused one-pass
+  // kernel (POST == 1): output k of the forward transform is multiplied by
+  // filt[k].  Last pass of a multi-pass plan (j-fast in, c-fast out), when
+  // filt != NULL: the element stored at offset o from `out` is multiplied by
+  // filt[o & filt_mask] (filt_mask = N - 1, rows N apart) before the scaling.
+  const float2* filt;
+  long long filt_mask;
 };
 
 template <int R>
@@ -187,7 +195,14 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 
 // One pass S of the tile: gather, twiddle, R-point DFT, scatter (with the
 // barriers that separate it from its neighbours).
-template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int IDX = 0>
+//   PRE  0: first pass reads global memory; 1: two-CTA radix-2 split;
+//        2: first pass reads a TMA-staged box; 3: first pass reads the tile
+//        already in shared memory (natural order, sidx layout), no conj_in.
+//   POST 0: last pass stores to global memory; 1: last pass multiplies
+//        output k by filt[k], conjugates it and leaves it in shared memory
+//        (natural order) for a following PRE == 3 transform.
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int IDX = 0,
+          int POST = 0>
 __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                           const TileArgs& a, const float2* gin, float2* gout,
                                           long long col0, long long bidx, const float2* epi_tab) {
@@ -215,7 +230,14 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   }
 
   // ---- gather the R inputs of each butterfly ----
-  if constexpr (FIRST) {
+  if constexpr (FIRST && PRE == 3) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const float2* rp = sm + cc[i] * LP + pidx(jj[i]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i * R + r] = rp[pidx_c(r * LR)];
+    }
+  } else if constexpr (FIRST) {
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const bool ok = (col0 + cc[i]) < a.ncols;
@@ -284,7 +306,21 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   for (int i = 0; i < NB; ++i) dft_fwd<R>(v + i * R);
 
   // ---- scatter outputs ----
-  if constexpr (LAST) {
+  if constexpr (LAST && POST == 1) {
+    static_assert(NB == 1 && IDX == 0 && !OUT_CF, "fused filter pass: contiguous rows");
+    // output k = j + q*NS of column c: conj(filt[k] * X[k]) into shared memory
+    const int c = cc[0], j = jj[0];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const float2 z = cmul(v[q], __ldg(a.filt + j + q * NS));
+      v[q] = make_float2(z.x, -z.y);
+    }
+    __syncthreads();   // all reads of this pass are done
+    float2* wp = sm + c * LP + pidx(j);
+#pragma unroll
+    for (int q = 0; q < R; ++q) wp[pidx_c(q * NS)] = v[q];
+    __syncthreads();
+  } else if constexpr (LAST) {
     static_assert(NB == 1, "last pass is radix-16 (or the whole length)");
     // After the last pass NS = L/R and j < NS: output index k = j + q*NS.
     const int c = cc[0], j = jj[0];
@@ -299,6 +335,16 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       const float2 base = cmul(__ldg(a.ft_lo + (m & mask)), __ldg(a.ft_hi + (m >> a.ft_s)));
 #pragma unroll
       for (int q = 0; q < R; ++q) v[q] = cmul(v[q], cmul(base, epi_tab[c * 16 + q]));
+    }
+    if constexpr (!IN_CF && OUT_CF && !OFFS && PRE == 0) {
+      if (a.filt) {
+        // multi-pass range compression: the stored element's offset from
+        // `out` modulo N is its frequency index
+        const long long o = (long long)(gout - a.out) + c * a.out_sc + (long long)j * a.out_sn;
+        const long long st = (long long)NS * a.out_sn;
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = cmul(v[q], __ldg(a.filt + ((o + q * st) & a.filt_mask)));
+      }
     }
     if (a.scale_out) {
 #pragma unroll
@@ -319,7 +365,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       }
     }
   } else {
-    if constexpr (!FIRST) __syncthreads();   // all reads of this pass are done
+    if constexpr (!FIRST || PRE == 3) __syncthreads();   // all reads of this pass are done
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = jj[i];
@@ -337,13 +383,13 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   }
 }
 
-template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0>
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int POST = 0>
 __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                            const TileArgs& a, const float2* gin, float2* gout,
                                            long long col0, long long bidx, const float2* epi_tab) {
-  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS, PRE>(v, sm, a, gin, gout, col0, bidx, epi_tab);
+  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS, PRE, 0, POST>(v, sm, a, gin, gout, col0, bidx, epi_tab);
   if constexpr (S + 1 < TileCfg<LG, C, IN_CF, OUT_CF>::NST)
-    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS, PRE>(v, sm, a, gin, gout, col0, bidx, epi_tab);
+    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS, PRE, POST>(v, sm, a, gin, gout, col0, bidx, epi_tab);
 }
 
 // One tile of a pass: tile index `tile` of the launch described by `a`, using
@@ -407,6 +453,37 @@ __global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
     tile_fft_kernel(const TileArgs a) {
   extern __shared__ float2 smem[];
   tile_body<LG, C, IN_CF, OUT_CF>(a, (long long)blockIdx.x, smem);
+}
+
+// Range compression of C contiguous rows per CTA (fast convolution, the
+// FFT-based SAR step of Sec. 3 and Sec. 4): y = IDFT(H * DFT(x)) with one
+// read and one write of every value.  The forward transform (Eq. 1) ends in
+// shared memory as conj(H X); a second forward transform of it, conjugated
+// and scaled by 1/L on the store (a.sx = 1/L, a.sy = -1/L), is Eq. 2 of H X.
+// Shared memory: C * LP entries (also for lengths of a single pass).
+template <int LG, int C>
+__global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T) tile_rc_kernel(const TileArgs a) {
+  extern __shared__ float2 smem[];
+  float2 v[TileCfg<LG, C, false, false>::P];
+  {
+    const long long tile = blockIdx.x;
+    const long long b = tile / a.tiles_per_batch;
+    const long long g = tile - b * a.tiles_per_batch;
+    const float2* gin = a.in + b * a.in_bstride + g * a.in_gstride;
+    tile_stage<LG, C, false, false, 0, false, 0, 1>(v, smem, a, gin, nullptr, g * C, b, nullptr);
+  }
+  {
+    // The tile index is read again, opaquely, so that the output address is
+    // computed here instead of being held in registers through the first
+    // transform (which spills at 2^14, 64 registers per thread).
+    unsigned t;
+    asm volatile("mov.u32 %0, %%ctaid.x;" : "=r"(t));
+    const long long tile = t;
+    const long long b = tile / a.tiles_per_batch;
+    const long long g = tile - b * a.tiles_per_batch;
+    float2* gout = a.out + b * a.out_bstride + g * a.out_gstride;
+    tile_stage<LG, C, false, false, 0, false, 3, 0>(v, smem, a, nullptr, gout, g * C, b, nullptr);
+  }
 }
 
 }  // namespace gbfft

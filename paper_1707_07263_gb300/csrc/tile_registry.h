@@ -36,6 +36,10 @@ int coltma_launch(const TileKernelInfo* k, const TileArgs& a, long long ntiles, 
 // Two-CTA radix-2 split kernels (tile_fft_dif2_kernel) for half length 2^lg.
 const TileKernelInfo* tile_kernel_dif2(int lg);
 
+// Fused range-compression kernels (tile_rc_kernel), lengths 2^1..2^14 with
+// jj_cols(lg) rows per CTA.
+const TileKernelInfo* tile_kernel_rc(int lg);
+
 // Returns NULL when (map, lg, C) was not compiled.
 const TileKernelInfo* tile_kernel(int map, int lg, int C);
 

@@ -82,6 +82,8 @@ def test_plan_create_many_rejects(lib):
 def test_null_plan_calls(lib):
     assert lib.fft_exec(None, None, None, None) == -1
     assert lib.fft_exec_dir(None, None, None, 0, None) == -1
+    assert lib.fft_exec_filter(None, None, None, None, None) == -1
+    assert lib.fft_pointer_usable(None, 8) == -1
     assert lib.fft_plan_workspace_bytes(None) == 0
     assert lib.fft_plan_set_workspace(None, None) == -1
     assert lib.fft_plan_launches(None) == 0
@@ -94,3 +96,5 @@ def test_python_api_fails_loudly_without_cuda_tensor():
     import paper_1707_07263_gb300 as gb
     with pytest.raises(TypeError):
         gb.fft(torch.zeros(16, dtype=torch.complex64))   # CPU tensor: no fallback
+    with pytest.raises(TypeError):
+        gb.range_compress(torch.zeros(16, dtype=torch.complex64), torch.zeros(16, dtype=torch.complex64))
