@@ -30,7 +30,7 @@ constexpr int kMaxPasses = 4;
 
 enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3 };
 
-cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s);
+cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false);
 cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);
 
 }  // namespace gbfft
@@ -52,6 +52,7 @@ struct fft_plan {
   const gbfft::TileKernelInfo* ktma;  // persistent TMA-staged single-pass kernel (or NULL)
   const gbfft::TileKernelInfo* kdif2; // two-CTA radix-2 split kernel (or NULL)
   const gbfft::TileKernelInfo* krc;   // fused range-compression kernel of the length (or NULL)
+  void* d_rctw;                       // its remainder-last stage table (NULL: the length's own table)
   const float2* pre_tw;               // its W_N^n table, n < N/2
   long long tma_grid;                 // its resident-CTA grid
 

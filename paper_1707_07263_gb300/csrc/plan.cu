@@ -167,6 +167,7 @@ static void free_plan(fft_plan* p) {
   if (p->fused) fused_plan_free(p);
   if (p->ws_owned && p->ws) cudaFree(p->ws);
   if (p->d_tc) cudaFree(p->d_tc);
+  if (p->d_rctw) cudaFree(p->d_rctw);
   if (p->d_tables) cudaFree(p->d_tables);
   delete p;
 }
@@ -336,6 +337,7 @@ static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const fl
     a.in_sc = a.out_sc = L;
     a.in_sn = a.out_sn = 1;
     a.ncols = p->batch;
+    a.tw_rev = p->d_rctw ? (const float2*)p->d_rctw : p->tw1;
     a.filt = filt;
     a.filt_mask = L - 1;
     a.scale_out = 1;
@@ -449,6 +451,13 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
       p->krc = tile_kernel_rc(lgN);
       rc = prepare_kernel(p->krc);
       if (rc) return rc;
+      if (lgN % 4 != 0 && lgN > 4) {
+        // the fused kernel's second transform runs the remainder pass last
+        if (cudaMalloc(&p->d_rctw, (size_t)stage_tw_size(lgN, true) * 8) != cudaSuccess) return FFT_ERR_ALLOC;
+        if (launch_gen_stage_twiddles((float2*)p->d_rctw, lgN, 0, true) != cudaSuccess ||
+            cudaStreamSynchronize(0) != cudaSuccess)
+          return FFT_ERR_CUDA;
+      }
     }
     // Two CTAs per transform (radix-2 split) is an autotuner option: with the
     // linear shared-memory addressing the one-CTA pass measures faster at

@@ -41,24 +41,31 @@
 namespace gbfft {
 
 // ---------------------------------------------------------------------------
-// Radix schedule for L = 2^LG: remainder pass first, then radix-16 passes.
+// Radix schedule for L = 2^LG: the remainder pass first, then radix-16 passes
+// (rev = false, every kernel); or the radix-16 passes first and the remainder
+// pass last (rev = true: the second transform of the fused range-compression
+// kernel, whose first pass then needs exactly the points that the first
+// transform's last pass left in each thread).
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int radix_nst(int lg) { return (lg + 3) / 4; }
-__host__ __device__ constexpr int radix_lgr(int lg, int s) {
-  return (lg % 4 != 0 && s == 0) ? (lg % 4) : 4;
+__host__ __device__ constexpr int radix_lgr(int lg, int s, bool rev = false) {
+  return (lg % 4 != 0 && s == (rev ? radix_nst(lg) - 1 : 0)) ? (lg % 4) : 4;
 }
-__host__ __device__ constexpr int radix_lgns(int lg, int s) {
-  return s == 0 ? 0 : radix_lgns(lg, s - 1) + radix_lgr(lg, s - 1);
+__host__ __device__ constexpr int radix_lgns(int lg, int s, bool rev = false) {
+  return s == 0 ? 0 : radix_lgns(lg, s - 1, rev) + radix_lgr(lg, s - 1, rev);
 }
 // Offset (in complex entries) of pass s's twiddle basis in the per-length
 // table.  Pass s with Ns > 1 stores lgr(s) rows of Ns entries:
 //   row e (e = 0..lgr-1), column k:  W_{Ns*R}^{(2^e) * k}.
-__host__ __device__ constexpr int stage_tw_off(int lg, int s) {
+__host__ __device__ constexpr int stage_tw_off(int lg, int s, bool rev = false) {
   return s == 0 ? 0
-                : stage_tw_off(lg, s - 1) +
-                      ((radix_lgns(lg, s - 1) > 0) ? radix_lgr(lg, s - 1) * (1 << radix_lgns(lg, s - 1)) : 0);
+                : stage_tw_off(lg, s - 1, rev) +
+                      ((radix_lgns(lg, s - 1, rev) > 0) ? radix_lgr(lg, s - 1, rev) * (1 << radix_lgns(lg, s - 1, rev))
+                                                        : 0);
 }
-__host__ __device__ constexpr int stage_tw_size(int lg) { return stage_tw_off(lg, radix_nst(lg)); }
+__host__ __device__ constexpr int stage_tw_size(int lg, bool rev = false) {
+  return stage_tw_off(lg, radix_nst(lg), rev);
+}
 
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
@@ -168,6 +175,8 @@ struct TileArgs {
   // filt[o & filt_mask] (filt_mask = N - 1, rows N apart) before the scaling.
   const float2* filt;
   long long filt_mask;
+  // Stage table of the remainder-last schedule (REV passes).
+  const float2* tw_rev;
 };
 
 template <int R>
@@ -196,20 +205,23 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 // One pass S of the tile: gather, twiddle, R-point DFT, scatter (with the
 // barriers that separate it from its neighbours).
 //   PRE  0: first pass reads global memory; 1: two-CTA radix-2 split;
-//        2: first pass reads a TMA-staged box; 3: first pass reads the tile
-//        already in shared memory (natural order, sidx layout), no conj_in.
-//   POST 0: last pass stores to global memory; 1: last pass multiplies
-//        output k by filt[k], conjugates it and leaves it in shared memory
-//        (natural order) for a following PRE == 3 transform.
+//        2: first pass reads a TMA-staged box; 4: the first pass's inputs are
+//        already in registers (left there by a POST == 2 transform), no conj_in.
+//   POST 0: last pass stores to global memory; 2: last pass multiplies output
+//        k by filt[k] and conjugates it, in registers.
+//   REV: remainder-last radix schedule (tables from a.tw_rev).  A POST == 2
+//        transform (radix-16 last pass: thread j holds k = j + q*L/16) feeds a
+//        PRE == 4, REV transform (radix-16 first pass: thread j reads n = j +
+//        r*L/16) without an exchange; lengths below 16 are one pass either way.
 template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int IDX = 0,
-          int POST = 0>
+          int POST = 0, bool REV = false>
 __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                           const TileArgs& a, const float2* gin, float2* gout,
                                           long long col0, long long bidx, const float2* epi_tab) {
   using Cfg = TileCfg<LG, C, IN_CF, OUT_CF, IDX>;
   constexpr int L = Cfg::L, P = Cfg::P, T = Cfg::T, NST = Cfg::NST, LP = Cfg::LP;
-  constexpr int LGR = radix_lgr(LG, S), R = 1 << LGR;
-  constexpr int LGNS = radix_lgns(LG, S), NS = 1 << LGNS;
+  constexpr int LGR = radix_lgr(LG, S, REV), R = 1 << LGR;
+  constexpr int LGNS = radix_lgns(LG, S, REV), NS = 1 << LGNS;
   constexpr bool FIRST = (S == 0), LAST = (S == NST - 1);
   constexpr bool CF = (FIRST && IN_CF) || (LAST && OUT_CF);
   constexpr int NB = P / R;   // butterflies per thread in this pass
@@ -230,13 +242,8 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   }
 
   // ---- gather the R inputs of each butterfly ----
-  if constexpr (FIRST && PRE == 3) {
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      const float2* rp = sm + cc[i] * LP + pidx(jj[i]);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[i * R + r] = rp[pidx_c(r * LR)];
-    }
+  if constexpr (FIRST && PRE == 4) {
+    static_assert(NB == 1 && (R == 16 || R == L), "register hand-over needs a one-butterfly first pass");
   } else if constexpr (FIRST) {
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
@@ -296,7 +303,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
 
   // ---- twiddles W_{Ns*R}^{r*(j mod Ns)} ----
   if constexpr (NS > 1) {
-    const float2* t = a.tw + stage_tw_off(LG, S);
+    const float2* t = (REV ? a.tw_rev : a.tw) + stage_tw_off(LG, S, REV);
 #pragma unroll
     for (int i = 0; i < NB; ++i) apply_stage_twiddle<R>(v + i * R, t, NS, jj[i] & (NS - 1));
   }
@@ -306,20 +313,36 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   for (int i = 0; i < NB; ++i) dft_fwd<R>(v + i * R);
 
   // ---- scatter outputs ----
-  if constexpr (LAST && POST == 1) {
-    static_assert(NB == 1 && IDX == 0 && !OUT_CF, "fused filter pass: contiguous rows");
-    // output k = j + q*NS of column c: conj(filt[k] * X[k]) into shared memory
-    const int c = cc[0], j = jj[0];
+  if constexpr (LAST && POST == 2) {
+    static_assert(NB == 1 && IDX == 0 && !OUT_CF && !REV, "fused filter pass: contiguous rows");
+    // output k = j + q*NS stays in the thread as conj(filt[k] * X[k])
+    const int j = jj[0];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const float2 z = cmul(v[q], __ldg(a.filt + j + q * NS));
       v[q] = make_float2(z.x, -z.y);
     }
-    __syncthreads();   // all reads of this pass are done
-    float2* wp = sm + c * LP + pidx(j);
+  } else if constexpr (LAST && REV) {
+    static_assert(IDX == 0 && !OUT_CF && !OFFS && PRE != 1, "remainder-last schedule: contiguous rows");
+    // NB butterflies per thread; butterfly i writes k = j_i + q*NS of column c_i
 #pragma unroll
-    for (int q = 0; q < R; ++q) wp[pidx_c(q * NS)] = v[q];
-    __syncthreads();
+    for (int i = 0; i < NB; ++i) {
+      const int c = cc[i], j = jj[i];
+      if (a.scale_out) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[i * R + q] = make_float2(v[i * R + q].x * a.sx, v[i * R + q].y * a.sy);
+      }
+      if ((col0 + c) < a.ncols) {
+        float2* p = gout + c * a.out_sc + j;
+        if (a.stream_out) {
+#pragma unroll
+          for (int q = 0; q < R; ++q) __stcs(p + q * NS, v[i * R + q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < R; ++q) __stcg(p + q * NS, v[i * R + q]);
+        }
+      }
+    }
   } else if constexpr (LAST) {
     static_assert(NB == 1, "last pass is radix-16 (or the whole length)");
     // After the last pass NS = L/R and j < NS: output index k = j + q*NS.
@@ -365,7 +388,9 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       }
     }
   } else {
-    if constexpr (!FIRST || PRE == 3) __syncthreads();   // all reads of this pass are done
+    // all reads of this pass (or, for PRE == 4, of the previous transform's
+    // last pass) are done
+    if constexpr (!FIRST || PRE == 4) __syncthreads();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = jj[i];
@@ -383,13 +408,14 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   }
 }
 
-template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int POST = 0>
+template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int POST = 0,
+          bool REV = false>
 __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
                                            const TileArgs& a, const float2* gin, float2* gout,
                                            long long col0, long long bidx, const float2* epi_tab) {
-  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS, PRE, 0, POST>(v, sm, a, gin, gout, col0, bidx, epi_tab);
+  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS, PRE, 0, POST, REV>(v, sm, a, gin, gout, col0, bidx, epi_tab);
   if constexpr (S + 1 < TileCfg<LG, C, IN_CF, OUT_CF>::NST)
-    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS, PRE, POST>(v, sm, a, gin, gout, col0, bidx, epi_tab);
+    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS, PRE, POST, REV>(v, sm, a, gin, gout, col0, bidx, epi_tab);
 }
 
 // One tile of a pass: tile index `tile` of the launch described by `a`, using
@@ -457,10 +483,11 @@ __global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
 
 // Range compression of C contiguous rows per CTA (fast convolution, the
 // FFT-based SAR step of Sec. 3 and Sec. 4): y = IDFT(H * DFT(x)) with one
-// read and one write of every value.  The forward transform (Eq. 1) ends in
-// shared memory as conj(H X); a second forward transform of it, conjugated
-// and scaled by 1/L on the store (a.sx = 1/L, a.sy = -1/L), is Eq. 2 of H X.
-// Shared memory: C * LP entries (also for lengths of a single pass).
+// read and one write of every value.  The forward transform (Eq. 1) ends with
+// conj(H X) in registers; a second forward transform of it (remainder-last
+// schedule, which starts from those registers), conjugated and scaled by 1/L
+// on the store (a.sx = 1/L, a.sy = -1/L), is Eq. 2 of H X.
+// Shared memory: C * LP entries.
 template <int LG, int C>
 __global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T) tile_rc_kernel(const TileArgs a) {
   extern __shared__ float2 smem[];
@@ -470,7 +497,7 @@ __global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T) tile_rc_kerne
     const long long b = tile / a.tiles_per_batch;
     const long long g = tile - b * a.tiles_per_batch;
     const float2* gin = a.in + b * a.in_bstride + g * a.in_gstride;
-    tile_stage<LG, C, false, false, 0, false, 0, 1>(v, smem, a, gin, nullptr, g * C, b, nullptr);
+    tile_stage<LG, C, false, false, 0, false, 0, 2>(v, smem, a, gin, nullptr, g * C, b, nullptr);
   }
   {
     // The tile index is read again, opaquely, so that the output address is
@@ -482,7 +509,7 @@ __global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T) tile_rc_kerne
     const long long b = tile / a.tiles_per_batch;
     const long long g = tile - b * a.tiles_per_batch;
     float2* gout = a.out + b * a.out_bstride + g * a.out_gstride;
-    tile_stage<LG, C, false, false, 0, false, 3, 0>(v, smem, a, nullptr, gout, g * C, b, nullptr);
+    tile_stage<LG, C, false, false, 0, false, 4, 0, true>(v, smem, a, nullptr, gout, g * C, b, nullptr);
   }
 }
 

@@ -18,14 +18,15 @@ __device__ __forceinline__ float2 w_entry(long long m, long long M) {
 }
 
 // Stage table of length L = 2^lg: for pass s with Ns > 1, row e, column k
-// holds W_{Ns*R}^{2^e * k} at stage_tw_off(lg, s) + e*Ns + k.
-__global__ void gen_stage_twiddles(float2* tab, int lg) {
-  const int total = stage_tw_size(lg);
+// holds W_{Ns*R}^{2^e * k} at stage_tw_off(lg, s, rev) + e*Ns + k (rev: the
+// remainder-last schedule).
+__global__ void gen_stage_twiddles(float2* tab, int lg, bool rev) {
+  const int total = stage_tw_size(lg, rev);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     int s = 1;
-    while (s + 1 < radix_nst(lg) && idx >= stage_tw_off(lg, s + 1)) ++s;
-    const int local = idx - stage_tw_off(lg, s);
-    const int lgns = radix_lgns(lg, s), lgr = radix_lgr(lg, s);
+    while (s + 1 < radix_nst(lg) && idx >= stage_tw_off(lg, s + 1, rev)) ++s;
+    const int local = idx - stage_tw_off(lg, s, rev);
+    const int lgns = radix_lgns(lg, s, rev), lgr = radix_lgr(lg, s, rev);
     const int NS = 1 << lgns;
     const int e = local / NS, k = local % NS;
     const long long M = 1LL << (lgns + lgr);
@@ -41,12 +42,12 @@ __global__ void gen_power_twiddles(float2* tab, int lgN, long long count, long l
     tab[i] = w_entry((i * step) % N, N);
 }
 
-cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s) {
-  const int total = stage_tw_size(lg);
+cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev) {
+  const int total = stage_tw_size(lg, rev);
   if (total == 0) return cudaSuccess;
   const int threads = 256;
   const int blocks = (total + threads - 1) / threads;
-  gen_stage_twiddles<<<blocks, threads, 0, s>>>(tab, lg);
+  gen_stage_twiddles<<<blocks, threads, 0, s>>>(tab, lg, rev);
   return cudaGetLastError();
 }
 
