@@ -518,13 +518,23 @@ def run_case(args):
     x = torch.randn(n * batch, dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if args.filter:
+        # range compression with a random filter (fft_exec_filter)
+        H = torch.randn(n, dtype=torch.complex64, device="cuda")
+
+        def one():
+            _lib.check(lib.fft_exec_filter(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                           ctypes.c_void_p(H.data_ptr()), s))
+    else:
+        def one():
+            _lib.check(lib.fft_exec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), s))
     for _ in range(args.warmup):
-        _lib.check(lib.fft_exec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), s))
+        one()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        _lib.check(lib.fft_exec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), s))
+        one()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
@@ -748,6 +758,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--dir", type=int, default=0)
     ap.add_argument("--prec", type=int, default=0)
+    ap.add_argument("--filter", action="store_true", help="with --case: range compression instead of the FFT")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -481,6 +481,12 @@ __global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
   tile_body<LG, C, IN_CF, OUT_CF>(a, (long long)blockIdx.x, smem);
 }
 
+// Resident CTAs per SM the fused kernel is compiled for: 64 registers per
+// thread at every size (measured on GB300: more registers than the default
+// heuristic picks speed up 2^13 and 2^14; 48 at 256 threads spills and
+// does not help 2^12).
+__host__ __device__ constexpr int rc_min_blocks(int threads) { return threads <= 256 ? 4 : (threads <= 512 ? 2 : 1); }
+
 // Range compression of C contiguous rows per CTA (fast convolution, the
 // FFT-based SAR step of Sec. 3 and Sec. 4): y = IDFT(H * DFT(x)) with one
 // read and one write of every value.  The forward transform (Eq. 1) ends with
@@ -489,7 +495,8 @@ __global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
 // on the store (a.sx = 1/L, a.sy = -1/L), is Eq. 2 of H X.
 // Shared memory: C * LP entries.
 template <int LG, int C>
-__global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T) tile_rc_kernel(const TileArgs a) {
+__global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T, rc_min_blocks(TileCfg<LG, C, false, false>::T))
+    tile_rc_kernel(const TileArgs a) {
   extern __shared__ float2 smem[];
   float2 v[TileCfg<LG, C, false, false>::P];
   {
