@@ -67,6 +67,16 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def single_kernel_name(lib, h) -> str:
+    """The kernel a one-launch plan runs, from its configuration."""
+    from paper_1707_07263_gb300 import _lib
+    c = _lib.FftPlanConfig()
+    _lib.check(lib.fft_plan_get_config(h, ctypes.byref(c)))
+    if c.halves == 2:
+        return "tile_fft_dif2_kernel"
+    return {1: "tile_fft_tma_kernel", 2: "tile_fft_pf_kernel"}.get(c.tma, "tile_fft_kernel")
+
+
 def ncu_traffic(kernel_key: str):
     """DRAM bytes per launch of `kernel_key` from the committed ncu summary, or
     None when the kernels changed since the counters were taken."""
@@ -318,7 +328,8 @@ def run_gpu(args):
     # average per-launch duration of the dominant plan's kernels
     achieved = bytes_launch / (per_item_ms[dom] / nl * 1e-3) / 1e9
     lg = int(np.log2(n))
-    traffic = ncu_traffic(f"tile_fft_jj_lg{lg}") if nl == 1 else None
+    kname = single_kernel_name(lib, plans[(n, batch)][0]) if nl == 1 else "multi-pass"
+    traffic = ncu_traffic(f"{kname}_lg{lg}") if nl == 1 else None
     per_size = {}
     for i, (lab, nn, bb, dd) in enumerate(items):
         gbs = 16.0 * nn * bb / (per_item_ms[i] * 1e-3) / 1e9
@@ -443,7 +454,7 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": f"tile_fft_kernel (JJ, L=2^{lg}, {label})",
+                     "kernel": f"{kname} (L=2^{lg}, {label})",
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"},
         "per_size": per_size,

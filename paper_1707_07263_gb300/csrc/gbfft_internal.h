@@ -51,8 +51,11 @@ struct fft_plan {
   const gbfft::TileKernelInfo* k2;
   const gbfft::TileKernelInfo* ktma;  // persistent TMA-staged single-pass kernel (or NULL)
   const gbfft::TileKernelInfo* kdif2; // two-CTA radix-2 split kernel (or NULL)
+  const gbfft::TileKernelInfo* kpf;   // persistent L2-prefetching single-pass kernel (or NULL)
+  long long pf_grid;                  // its resident-CTA grid
   const gbfft::TileKernelInfo* krc;   // fused range-compression kernel of the length (or NULL)
   void* d_rctw;                       // its remainder-last stage table (NULL: the length's own table)
+  long long rc_grid;                  // its grid when persistent (0: one tile per CTA)
   const float2* pre_tw;               // its W_N^n table, n < N/2
   long long tma_grid;                 // its resident-CTA grid
 

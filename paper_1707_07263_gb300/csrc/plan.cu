@@ -263,6 +263,15 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
   a.ncols = p->batch;
   a.conj_in = x.conj;
   set_out_xf(a, x);
+  if (p->kpf) {
+    long long ntiles = a.tiles_per_batch;
+    const long long grid = p->pf_grid < ntiles ? p->pf_grid : ntiles;
+    void* args[] = {(void*)&a, (void*)&ntiles};
+    return cudaLaunchKernel(p->kpf->fn, dim3((unsigned)grid), dim3(p->kpf->threads), args,
+                            (size_t)p->kpf->smem_bytes, s) == cudaSuccess
+               ? FFT_OK
+               : FFT_ERR_CUDA;
+  }
   return launch_tile(p->k1, a, a.tiles_per_batch, s);
 }
 
@@ -343,7 +352,14 @@ static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const fl
     a.scale_out = 1;
     a.sx = inv_n;
     a.sy = -inv_n;
-    return launch_tile(p->krc, a, a.tiles_per_batch, s);
+    long long ntiles = a.tiles_per_batch;
+    const long long grid = (p->rc_grid > 0 && p->rc_grid < ntiles) ? p->rc_grid : ntiles;
+    if (grid > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
+    void* args[] = {(void*)&a, (void*)&ntiles};
+    return cudaLaunchKernel(p->krc->fn, dim3((unsigned)grid), dim3(p->krc->threads), args,
+                            (size_t)p->krc->smem_bytes, s) == cudaSuccess
+               ? FFT_OK
+               : FFT_ERR_CUDA;
   }
   if (p->kind != KIND_FOURSTEP || p->fused || p->npass < 2) return FFT_ERR_UNSUPPORTED;
   if (p->pass[p->npass - 1].k->map != MAP_JC) return FFT_ERR_UNSUPPORTED;
@@ -451,6 +467,16 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
       p->krc = tile_kernel_rc(lgN);
       rc = prepare_kernel(p->krc);
       if (rc) return rc;
+      if (rc_persistent(lgN)) {
+        int per_sm = 0, sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->krc->fn, p->krc->threads,
+                                                          (size_t)p->krc->smem_bytes) != cudaSuccess ||
+            per_sm < 1)
+          return FFT_ERR_CUDA;
+        p->rc_grid = (long long)per_sm * sms;
+      }
       if (lgN % 4 != 0 && lgN > 4) {
         // the fused kernel's second transform runs the remainder pass last
         if (cudaMalloc(&p->d_rctw, (size_t)stage_tw_size(lgN, true) * 8) != cudaSuccess) return FFT_ERR_ALLOC;
@@ -486,6 +512,27 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
           cudaStreamSynchronize(0) != cudaSuccess)
         return FFT_ERR_CUDA;
       return FFT_OK;
+    }
+    // Persistent register path with an L2 prefetch of the next transform:
+    // measured on GB300 it pays where one CTA fills an SM (2^14: 279 -> 248
+    // us per 2^26 points), not at 2^13 (two CTAs per SM already overlap)
+    // nor at 2^12 (its loop costs a resident CTA).
+    const int env_pf = env_int("GBFFT_PF", -1);
+    const bool want_pf = tile_kernel_pf(lgN) && p->prec == FFT_PREC_FP32 && cfg->halves != 2 &&
+                         (cfg->tma == 2 || (cfg->tma < 0 && (env_pf >= 0 ? env_pf > 0 : lgN == 14)));
+    if (want_pf) {
+      p->kpf = tile_kernel_pf(lgN);
+      rc = prepare_kernel(p->kpf);
+      if (rc) return rc;
+      int per_sm = 0, sms = 0, dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kpf->fn, p->kpf->threads,
+                                                        (size_t)p->kpf->smem_bytes) != cudaSuccess ||
+          per_sm < 1)
+        return FFT_ERR_CUDA;
+      p->pf_grid = (long long)per_sm * sms;
+      return build_tables(p, lgN, 0, 0);
     }
     const bool want_tma =
         cfg->tma < 0 ? (lgN >= 9 && lgN <= 11 && !env_int("GBFFT_NO_TMA", 0)) : (cfg->tma > 0 && lgN >= 1);
@@ -854,7 +901,7 @@ int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
     out->npass = 1;
     out->lg1 = p->lg;
     out->c1 = p->c1;
-    out->tma = p->ktma ? 1 : 0;
+    out->tma = p->ktma ? 1 : (p->kpf ? 2 : 0);
     out->halves = p->kdif2 ? 2 : 1;
   } else if (p->kind == KIND_FOURSTEP) {
     out->npass = p->npass ? p->npass : 2;

@@ -481,6 +481,30 @@ __global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
   tile_body<LG, C, IN_CF, OUT_CF>(a, (long long)blockIdx.x, smem);
 }
 
+// Persistent single-pass variant for one transform per CTA (C == 1, contiguous
+// rows): CTA b takes tiles b, b + grid, ...  Before transforming a tile, its
+// threads ask L2 for the next one (prefetch.global.L2, one 128-byte line per
+// thread per step), so that the next load phase hits L2 and the DRAM reads
+// overlap this tile's passes instead of following them.
+template <int LG>
+__global__ void __launch_bounds__(TileCfg<LG, 1, false, false>::T)
+    tile_fft_pf_kernel(const TileArgs a, long long ntiles) {
+  extern __shared__ float2 smem[];
+  using Cfg = TileCfg<LG, 1, false, false>;
+  constexpr int BYTES = Cfg::L * 8;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long nt = t + gridDim.x;
+    if (nt < ntiles) {
+      const char* p = (const char*)(a.in + nt * a.in_gstride);
+#pragma unroll
+      for (int off = threadIdx.x * 128; off < BYTES; off += Cfg::T * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+    }
+    tile_body<LG, 1, false, false>(a, t, smem);
+    __syncthreads();   // the next tile's first exchange overwrites this one's
+  }
+}
+
 // Resident CTAs per SM the fused kernel is compiled for: 64 registers per
 // thread at every size (measured on GB300: more registers than the default
 // heuristic picks speed up 2^13 and 2^14; 48 at 256 threads spills and
@@ -494,29 +518,45 @@ __host__ __device__ constexpr int rc_min_blocks(int threads) { return threads <=
 // schedule, which starts from those registers), conjugated and scaled by 1/L
 // on the store (a.sx = 1/L, a.sy = -1/L), is Eq. 2 of H X.
 // Shared memory: C * LP entries.
+// One CTA per SM at 2^14: the kernel is persistent there and prefetches the
+// next row into L2 (as tile_fft_pf_kernel); shorter rows take one tile per CTA.
+__host__ __device__ constexpr bool rc_persistent(int lg) { return lg == 14; }
+
 template <int LG, int C>
 __global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T, rc_min_blocks(TileCfg<LG, C, false, false>::T))
-    tile_rc_kernel(const TileArgs a) {
+    tile_rc_kernel(const TileArgs a, long long ntiles) {
   extern __shared__ float2 smem[];
-  float2 v[TileCfg<LG, C, false, false>::P];
-  {
-    const long long tile = blockIdx.x;
-    const long long b = tile / a.tiles_per_batch;
-    const long long g = tile - b * a.tiles_per_batch;
-    const float2* gin = a.in + b * a.in_bstride + g * a.in_gstride;
-    tile_stage<LG, C, false, false, 0, false, 0, 2>(v, smem, a, gin, nullptr, g * C, b, nullptr);
-  }
-  {
-    // The tile index is read again, opaquely, so that the output address is
-    // computed here instead of being held in registers through the first
-    // transform (which spills at 2^14, 64 registers per thread).
-    unsigned t;
-    asm volatile("mov.u32 %0, %%ctaid.x;" : "=r"(t));
-    const long long tile = t;
-    const long long b = tile / a.tiles_per_batch;
-    const long long g = tile - b * a.tiles_per_batch;
-    float2* gout = a.out + b * a.out_bstride + g * a.out_gstride;
-    tile_stage<LG, C, false, false, 0, false, 4, 0, true>(v, smem, a, nullptr, gout, g * C, b, nullptr);
+  using Cfg = TileCfg<LG, C, false, false>;
+  float2 v[Cfg::P];
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if constexpr (rc_persistent(LG)) {
+      const long long nt = t + gridDim.x;
+      if (nt < ntiles) {
+        const char* p = (const char*)(a.in + nt * a.in_gstride);
+#pragma unroll
+        for (int off = threadIdx.x * 128; off < C * Cfg::L * 8; off += Cfg::T * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+      }
+    }
+    {
+      const long long b = t / a.tiles_per_batch;
+      const long long g = t - b * a.tiles_per_batch;
+      const float2* gin = a.in + b * a.in_bstride + g * a.in_gstride;
+      tile_stage<LG, C, false, false, 0, false, 0, 2>(v, smem, a, gin, nullptr, g * C, b, nullptr);
+    }
+    {
+      // The tile index is passed through an opaque move, so that the output
+      // address is computed here instead of being held in registers through
+      // the first transform (which spills at 2^14, 64 registers per thread).
+      long long tt;
+      asm volatile("mov.b64 %0, %1;" : "=l"(tt) : "l"(t));
+      const long long b = tt / a.tiles_per_batch;
+      const long long g = tt - b * a.tiles_per_batch;
+      float2* gout = a.out + b * a.out_bstride + g * a.out_gstride;
+      tile_stage<LG, C, false, false, 0, false, 4, 0, true>(v, smem, a, nullptr, gout, g * C, b, nullptr);
+    }
+    if constexpr (!rc_persistent(LG)) break;
+    __syncthreads();   // the next tile's first exchange overwrites this one's
   }
 }
 

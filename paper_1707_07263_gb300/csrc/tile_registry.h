@@ -36,6 +36,10 @@ int coltma_launch(const TileKernelInfo* k, const TileArgs& a, long long ntiles, 
 // Two-CTA radix-2 split kernels (tile_fft_dif2_kernel) for half length 2^lg.
 const TileKernelInfo* tile_kernel_dif2(int lg);
 
+// Persistent single-pass kernels with an L2 prefetch of the next transform,
+// lengths 2^12..2^14 (one transform per CTA); signature void(TileArgs, long long).
+const TileKernelInfo* tile_kernel_pf(int lg);
+
 // Fused range-compression kernels (tile_rc_kernel), lengths 2^1..2^14 with
 // jj_cols(lg) rows per CTA.
 const TileKernelInfo* tile_kernel_rc(int lg);

@@ -50,6 +50,10 @@ static std::vector<fft_plan_config> candidates(int lgN) {
     v.push_back(c);
     c.tma = 1;
     v.push_back(c);
+    if (lgN >= 12) {
+      c.tma = 2;  // persistent register path with an L2 prefetch of the next transform
+      v.push_back(c);
+    }
     c.tma = 0;
     c.halves = 2;  // rejected where no split kernel exists
     v.push_back(c);

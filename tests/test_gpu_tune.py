@@ -55,6 +55,10 @@ def run_cfg(lib, x: np.ndarray, cfg: dict) -> np.ndarray:
     (12, {"npass": 1, "halves": 2}),
     (13, {"npass": 1, "halves": 2}),
     (14, {"npass": 1, "halves": 2}),
+    (12, {"npass": 1, "tma": 2}),
+    (13, {"npass": 1, "tma": 2}),
+    (14, {"npass": 1, "tma": 2}),
+    (14, {"npass": 1, "tma": 0}),
 ])
 def test_explicit_configs(lib, lg, cfg):
     n = 1 << lg
@@ -82,6 +86,29 @@ def test_two_cta_split_directions(lib, lg, d):
     lib.fft_destroy(h)
     x64 = x.astype(np.complex128)
     ref = {1: oracle.fft(x64, oracle.INVERSE), 2: oracle.fft(x64, oracle.ADJOINT),
+           3: oracle.fft(x64, oracle.FORWARD) / n}[d]
+    assert oracle.rel_l2_rows(out.cpu().numpy(), ref).max() <= 5e-7 * lg
+
+
+@pytest.mark.parametrize("lg,batch,d", [(14, 333, 0), (14, 457, 1), (13, 700, 2), (12, 1337, 3)])
+def test_prefetching_persistent_kernel_loops(lib, lg, batch, d):
+    """Persistent single pass with the L2 prefetch (tma = 2): more transforms
+    than resident CTAs, so every CTA loops and prefetches; every direction."""
+    n = 1 << lg
+    x = workloads.cgauss(n, batch, seed=8300 + lg + d)
+    c = _lib.FftPlanConfig.from_dict({"npass": 1, "tma": 2})
+    h = ctypes.c_void_p(lib.fft_plan_create_config(n, batch, d, 0, ctypes.byref(c)))
+    assert h.value
+    got_cfg = _lib.FftPlanConfig()
+    assert lib.fft_plan_get_config(h, ctypes.byref(got_cfg)) == 0 and got_cfg.tma == 2
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    assert lib.fft_exec(h, ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    torch.cuda.synchronize()
+    lib.fft_destroy(h)
+    x64 = x.astype(np.complex128)
+    ref = {0: oracle.fft(x64), 1: oracle.fft(x64, oracle.INVERSE), 2: oracle.fft(x64, oracle.ADJOINT),
            3: oracle.fft(x64, oracle.FORWARD) / n}[d]
     assert oracle.rel_l2_rows(out.cpu().numpy(), ref).max() <= 5e-7 * lg
 
