@@ -20,6 +20,11 @@ Functions (all FP64, numpy ``complex128`` in and out):
   application: every row becomes Eq. 2 applied to H * (Eq. 1 applied to the
   row), i.e. the circular convolution of the row with the inverse transform
   of H (for a matched filter H, the correlation with the transmitted pulse).
+* ``rfft(x)`` / ``irfft(X, n)`` -- transforms of real rows: Eq. 1 of a real
+  sequence keeps its n/2 + 1 non-redundant outputs (X[n-k] = conj(X[k]));
+  the inverse extends X[0..n/2] to the full Hermitian spectrum (the
+  imaginary parts of X[0] and X[n/2] do not enter) and returns the real part
+  of Eq. 2.
 * ``spectral_loss(x, w)`` and ``spectral_loss_grad(x, w)`` -- the loss
   L = sum_k |w_k X_k|^2 with X = Eq. 1 applied to x, and its gradient in
   PyTorch's convention (dL/dRe + i dL/dIm) = 2 F^H (w^2 * F x), where F^H is
@@ -148,6 +153,31 @@ def range_compress(x, H, lib=None) -> np.ndarray:
     if H.shape != x.shape[-1:]:
         raise ValueError(f"range_compress: filter of shape {H.shape} for rows of length {x.shape[-1]}")
     return transform(transform(x, FORWARD, lib) * H, INVERSE, lib)
+
+
+def rfft(x, lib=None) -> np.ndarray:
+    """X[k] = sum_n x[n] W_n^{nk} (Eq. 1) of real rows, k = 0..n/2."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[-1]
+    if n < 2 or n % 2:
+        raise ValueError(f"rfft: even length needed, got {n}")
+    return transform(x.astype(np.complex128), FORWARD, lib)[..., : n // 2 + 1]
+
+
+def irfft(X, n: int, lib=None) -> np.ndarray:
+    """Real rows x of length n whose Eq. 1 has X[0..n/2] as its first half:
+    Eq. 2 of the Hermitian extension F[k] = X[k] (k <= n/2), conj(X[n-k])
+    (k > n/2), with Im X[0] and Im X[n/2] set to zero, real part kept."""
+    X = np.asarray(X, dtype=np.complex128)
+    if n < 2 or n % 2 or X.shape[-1] != n // 2 + 1:
+        raise ValueError(f"irfft: {X.shape[-1]} values for length {n}")
+    h = n // 2
+    full = np.empty(X.shape[:-1] + (n,), dtype=np.complex128)
+    full[..., : h + 1] = X
+    full[..., 0] = X[..., 0].real
+    full[..., h] = X[..., h].real
+    full[..., h + 1:] = np.conj(X[..., 1:h][..., ::-1])
+    return transform(full, INVERSE, lib).real
 
 
 def spectral_loss(x, w) -> float:

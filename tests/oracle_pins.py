@@ -219,5 +219,54 @@ def check_range_compress(lib, rc=None):
     assert np.max(np.abs(np.delete(y, d))) < 0.5 * P, "matched-filter sidelobes"
 
 
+def check_real_transforms(lib, rf=None, irf=None):
+    """rfft / irfft against definitions written out here: the real-input DFT
+    sum, the cosine / sine closed forms, the round trip, and numpy's pocketfft
+    real transforms (an independent library)."""
+    if rf is None:
+        def rf(x):
+            return oracle.rfft(x, lib=lib)
+    if irf is None:
+        def irf(X, n):
+            return oracle.irfft(X, n, lib=lib)
+    # (a) brute force: X[k] = sum_n x[n] (cos(2 pi nk/N) - i sin(2 pi nk/N)), k <= N/2
+    for n in (2, 4, 8, 16, 64):
+        g = _rng(900 + n)
+        x = g.standard_normal((2, n))
+        t = np.arange(n)
+        ref = np.array([[np.sum(row * (np.cos(2 * np.pi * ((k * t) % n) / n) - 1j * np.sin(2 * np.pi * ((k * t) % n) / n)))
+                         for k in range(n // 2 + 1)] for row in x])
+        _close(rf(x), ref, 1e-12, f"rfft brute force N={n}")
+        _close(irf(ref, n), x, 1e-12, f"irfft of the brute-force spectrum N={n}")
+    # (b) closed forms: cos(2 pi m n / N) -> N/2 at k = m; sin -> -i N/2 at k = m;
+    #     the Nyquist cosine (-1)^n -> N at k = N/2
+    for n, m in ((32, 3), (1024, 100), (4096, 2047)):
+        t = np.arange(n)
+        c = np.zeros(n // 2 + 1, complex)
+        c[m] = n / 2
+        _close(rf(np.cos(2 * np.pi * ((m * t) % n) / n)), c, 1e-12, f"rfft cos N={n} m={m}")
+        sn = np.zeros(n // 2 + 1, complex)
+        sn[m] = -1j * n / 2
+        _close(rf(np.sin(2 * np.pi * ((m * t) % n) / n)), sn, 1e-12, f"rfft sin N={n} m={m}")
+        ny = np.zeros(n // 2 + 1, complex)
+        ny[n // 2] = n
+        _close(rf((-1.0) ** t), ny, 1e-12, f"rfft Nyquist N={n}")
+        _close(irf(c, n), np.cos(2 * np.pi * ((m * t) % n) / n), 1e-12, f"irfft cos N={n}")
+    # (c) imaginary parts of X[0] and X[N/2] do not enter the inverse
+    n = 64
+    X = _cvec(n // 2 + 1, seed=901)
+    Y = X.copy()
+    Y[0] += 5j
+    Y[-1] -= 3j
+    _close(irf(Y, n), irf(X, n), 1e-13, "irfft ignores Im X[0], Im X[N/2]")
+    # (d) round trip and numpy's real transforms
+    for n in (2, 128, 2048, 65536):
+        x = _rng(902 + n).standard_normal((2, n))
+        _close(irf(rf(x), n), x, 1e-12, f"irfft(rfft(x)) N={n}")
+        _close(rf(x), np.fft.rfft(x, axis=-1), 1e-13, f"rfft vs numpy N={n}")
+        X = _cvec(n // 2 + 1, seed=903 + n, batch=2)
+        _close(irf(X, n), np.fft.irfft(X, n, axis=-1), 1e-12, f"irfft vs numpy N={n}")
+
+
 ALL_CHECKS = (check_golden, check_small_by_hand, check_closed_forms, check_invariants,
-              check_dft_vs_fft, check_numpy, check_fft2, check_range_compress)
+              check_dft_vs_fft, check_numpy, check_fft2, check_range_compress, check_real_transforms)

@@ -149,3 +149,63 @@ def test_range_workload_compresses():
     delays = g.integers(0, n, size=(4, 1)).ravel()
     assert np.array_equal(np.argmax(y, axis=1), delays)
     assert np.all(y.max(axis=1) > 1000 * np.median(y, axis=1))
+
+
+# Plausible mistakes in the real-data transforms (planted in copies of the
+# functions, on the CPU); the real-transform pin must fail for each.
+def _irfft_no_scale(X, n):
+    X = np.asarray(X, dtype=np.complex128)
+    h = n // 2
+    full = np.empty(X.shape[:-1] + (n,), dtype=np.complex128)
+    full[..., : h + 1] = X
+    full[..., 0] = X[..., 0].real
+    full[..., h] = X[..., h].real
+    full[..., h + 1:] = np.conj(X[..., 1:h][..., ::-1])
+    return oracle.transform(full, oracle.ADJOINT).real
+
+
+def _irfft_no_conj(X, n):
+    X = np.asarray(X, dtype=np.complex128)
+    h = n // 2
+    full = np.empty(X.shape[:-1] + (n,), dtype=np.complex128)
+    full[..., : h + 1] = X
+    full[..., 0] = X[..., 0].real
+    full[..., h] = X[..., h].real
+    full[..., h + 1:] = X[..., 1:h][..., ::-1]
+    return oracle.transform(full, oracle.INVERSE).real
+
+
+def _irfft_unreversed(X, n):
+    X = np.asarray(X, dtype=np.complex128)
+    h = n // 2
+    full = np.empty(X.shape[:-1] + (n,), dtype=np.complex128)
+    full[..., : h + 1] = X
+    full[..., 0] = X[..., 0].real
+    full[..., h] = X[..., h].real
+    full[..., h + 1:] = np.conj(X[..., 1:h])
+    return oracle.transform(full, oracle.INVERSE).real
+
+
+REAL_MUTATIONS = {
+    "rfft_drops_nyquist": (lambda x: np.concatenate([oracle.rfft(x)[..., :-1], np.zeros(np.shape(x)[:-1] + (1,))],
+                                                   axis=-1), None),
+    "rfft_inverse_sign": (lambda x: oracle.transform(np.asarray(x, complex), oracle.ADJOINT)[..., : np.shape(x)[-1] // 2 + 1],
+                          None),
+    "irfft_no_scale": (None, _irfft_no_scale),
+    "irfft_no_conj": (None, _irfft_no_conj),
+    "irfft_unreversed": (None, _irfft_unreversed),
+}
+
+
+@pytest.mark.parametrize("name", sorted(REAL_MUTATIONS))
+def test_real_pin_catches_mutation(lib, name):
+    rf, irf = REAL_MUTATIONS[name]
+    with pytest.raises(AssertionError):
+        pins.check_real_transforms(lib, rf=rf, irf=irf)
+
+
+def test_real_transforms_reject_bad_lengths():
+    with pytest.raises(ValueError):
+        oracle.rfft(np.ones(7))
+    with pytest.raises(ValueError):
+        oracle.irfft(np.ones(5, complex), 16)
