@@ -23,7 +23,7 @@ Also printed on the same JSON line:
 
 ``--impl reference`` times the oracle instead (the deliberately slow CPU
 baseline) and prints the same line with "impl": "reference".
-Other workloads for measurement only: --workload large | tc | many | range.
+Other workloads for measurement only: --workload large | tc | many | range | real.
 """
 from __future__ import annotations
 
@@ -750,6 +750,47 @@ def run_measure(args):
         desc = ("SAR range compression IFFT(H * FFT(line)): 2^26/N lines of N samples, LFM echoes + CN(0,1) "
                 "noise, closed-form matched filter; fused = fft_exec_filter, unfused = FFT, torch multiply, "
                 "IFFT; cufft_torch = torch.fft (context)")
+    elif args.workload == "real":
+        # real-data transforms: 2^26 reals per launch, N reals per row
+        for lg in (12, 13, 14, 15, 16, 20):
+            n = 1 << lg
+            batch = TOTAL // n
+            xh = workloads.uniform(n, batch, seed=workloads.seed_for(7) + lg).real.astype(np.float32)
+            x = torch.from_numpy(xh).to(dev)
+            X = torch.empty(batch, n // 2 + 1, dtype=torch.complex64, device=dev)
+            y = torch.empty_like(x)
+            p = api.Plan("r2c", (n,), batch, device=dev)
+            fwd = _time_fn(torch, lambda: p.exec_ptr(x.data_ptr(), X.data_ptr(), 0, stream), args.steps,
+                           args.warmup, stream)
+            inv = _time_fn(torch, lambda: p.exec_ptr(X.data_ptr(), y.data_ptr(), 1, stream), args.steps,
+                           args.warmup, stream)
+
+            def cufft():
+                with torch.cuda.stream(stream):
+                    torch.fft.rfft(x)
+
+            cu = _time_fn(torch, cufft, args.steps, args.warmup, stream)
+
+            def cufft_inv():
+                with torch.cuda.stream(stream):
+                    torch.fft.irfft(X, n)
+
+            cui = _time_fn(torch, cufft_inv, args.steps, args.warmup, stream)
+            p.exec_ptr(x.data_ptr(), X.data_ptr(), 0, stream)
+            torch.cuda.synchronize()
+            rows = [0, batch // 2, batch - 1]
+            err = float(oracle.rel_l2_rows(X[rows].cpu().numpy(), oracle.rfft(xh[rows].astype(np.float64))).max())
+            # algorithmic bytes: N reals in (4 B each) and N/2 + 1 complex out (8 B each)
+            byt = (4.0 * n + 8.0 * (n // 2 + 1)) * batch
+            res.append({"n": n, "rows": batch, "rfft_us": round(fwd * 1e3, 1), "irfft_us": round(inv * 1e3, 1),
+                        "cufft_torch_rfft_us": round(cu * 1e3, 1), "cufft_torch_irfft_us": round(cui * 1e3, 1),
+                        "gflops_rfft": round(2.5 * n * lg * batch / (fwd * 1e-3) / 1e9, 1),
+                        "hbm_frac_rfft": round(byt / (fwd * 1e-3) / 1e9 / peak, 4),
+                        "hbm_frac_irfft": round(byt / (inv * 1e-3) / 1e9 / peak, 4),
+                        "launches": p.launches, "err_sampled": float(f"{err:.3e}")})
+            del p
+        desc = ("real-data transforms: 2^26 U[-1,1] reals per launch in rows of N; rfft -> N/2+1 complex, irfft "
+                "back; GFLOP/s counts 2.5 N log2 N per real row; cufft_torch = torch.fft.rfft (context)")
     print(json.dumps({"workload": args.workload, "desc": desc, "results": res,
                       "peak_hbm_gbs": peak}), flush=True)
 
@@ -760,7 +801,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range", "real"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -88,6 +88,24 @@ GBFFT_API fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec)
  * (Sec. 2.3.2: rows, then columns). */
 GBFFT_API fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int prec);
 
+/* Plan for `batch` real-data transforms of length n (power of two,
+ * 4 <= n <= 2^28; FP32 only, prec must be FFT_PREC_FP32).  Run it with
+ * fft_exec_dir:
+ *   FFT_FORWARD (real to complex): in = batch rows of n floats, out = batch
+ *     rows of n/2 + 1 complex64 values X[k] = Eq. 1 of the row, k = 0..n/2
+ *     (the other half is X[n-k] = conj X[k]).
+ *   FFT_INVERSE (complex to real): in = batch rows of n/2 + 1 complex64 values,
+ *     out = batch rows of n floats, Eq. 2 (with 1/n) of the Hermitian
+ *     extension; Im X[0] and Im X[n/2] are ignored.
+ * The row of n reals is read as n/2 complex values x[2m] + i x[2m+1] (Sec. 2.1
+ * splits a sequence into even and odd samples the same way); one complex
+ * transform of length n/2 and one split step give the result.  n <= 2^15: one
+ * fused kernel, one read and one write of every value.  Longer n: the complex
+ * plan plus one split kernel, with a workspace (fft_plan_workspace_bytes).
+ * Pointers 8-byte aligned, device memory or memory fft_pointer_usable accepts;
+ * in == out is not allowed.  Other directions return FFT_ERR_INVALID_ARG. */
+GBFFT_API fft_plan* fft_plan_create_r2c(int64_t n, int64_t batch, int prec);
+
 /* Plan for `count` 1-D transforms of uneven power-of-two lengths lengths[i]
  * (2^1..2^16), packed back to back: transform i starts at the prefix sum of
  * the lengths before it.  The host array is copied; the caller keeps it. */
@@ -192,7 +210,8 @@ GBFFT_API int64_t fft_plan_length(const fft_plan* plan);
 GBFFT_API int64_t fft_plan_batch(const fft_plan* plan);
 /* Number of kernel launches one fft_exec issues. */
 GBFFT_API int fft_plan_launches(const fft_plan* plan);
-/* Kind: 0 single on-chip pass, 1 four-step, 2 two-dimensional, 3 uneven batch. */
+/* Kind: 0 single on-chip pass, 1 four-step, 2 two-dimensional, 3 uneven batch,
+ * 4 real data. */
 GBFFT_API int fft_plan_kind(const fft_plan* plan);
 /* Human-readable plan summary into buf (NUL-terminated); returns FFT_OK. */
 GBFFT_API int fft_plan_describe(const fft_plan* plan, char* buf, size_t len);

@@ -14,7 +14,7 @@ from ._lib import (FFT_ADJOINT, FFT_FORWARD, FFT_INVERSE, FFT_PREC_FP32, FFT_PRE
 
 def __getattr__(name):
     # lazy: torch and the CUDA library are only touched when the API is used
-    if name in ("fft", "ifft", "fft2", "ifft2", "fft_many", "fft_host", "HostPipeline", "range_compress", "Plan", "get_plan",
+    if name in ("fft", "ifft", "fft2", "ifft2", "fft_many", "fft_host", "HostPipeline", "range_compress", "rfft", "irfft", "Plan", "get_plan",
                 "clear_plan_cache", "PREC"):
         from . import api
         return getattr(api, name)

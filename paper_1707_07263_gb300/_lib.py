@@ -50,6 +50,7 @@ SIGNATURES = {
     "fft_plan_create": (_vp, [_i64, _i64, _int, _int]),
     "fft_plan_create_2d": (_vp, [_i64, _i64, _i64, _int, _int]),
     "fft_plan_create_many": (_vp, [ctypes.POINTER(_i64), _i64, _int, _int]),
+    "fft_plan_create_r2c": (_vp, [_i64, _i64, _int]),
     "fft_exec": (_int, [_vp, _vp, _vp, _vp]),
     "fft_exec_dir": (_int, [_vp, _vp, _vp, _int, _vp]),
     "fft_destroy": (None, [_vp]),

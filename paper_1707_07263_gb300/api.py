@@ -61,6 +61,8 @@ class Plan:
                 h = self.lib.fft_plan_create(int(shape[0]), self.batch, self.dir, self.prec)
             elif kind == "2d":
                 h = self.lib.fft_plan_create_2d(int(shape[0]), int(shape[1]), self.batch, self.dir, self.prec)
+            elif kind == "r2c":
+                h = self.lib.fft_plan_create_r2c(int(shape[0]), self.batch, self.prec)
             elif kind == "many":
                 arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
                 self.lengths = [int(v) for v in lengths]
@@ -276,6 +278,80 @@ def range_compress(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
     if H.device != x.device:
         raise ValueError("x and H must be on the same device")
     return _RangeCompress.apply(x.contiguous(), H.detach().contiguous())
+
+
+def _run_real(x: torch.Tensor, n: int, dir: int) -> torch.Tensor:
+    """Real-to-complex (dir FORWARD: float32 rows of n -> complex64 rows of
+    n/2 + 1) or complex-to-real (dir INVERSE) through a cached real plan."""
+    rows = x.shape[:-1]
+    batch = 1
+    for d in rows:
+        batch *= int(d)
+    if dir == FORWARD:
+        out = torch.empty(rows + (n // 2 + 1,), dtype=torch.complex64, device=x.device)
+    else:
+        out = torch.empty(rows + (n,), dtype=torch.float32, device=x.device)
+    if batch == 0:
+        return out
+    p = get_plan("r2c", (n,), batch, "fp32", x.device)
+    p.exec_ptr(x.data_ptr(), out.data_ptr(), dir)
+    return out
+
+
+class _RFFT(torch.autograd.Function):
+    """X = rfft(x).  For real x the gradient is Re(sum_k g_k W^{-nk}) over the
+    kept outputs, i.e. n * irfft(G) with G = g except the interior bins
+    halved (irfft counts each of them twice)."""
+
+    @staticmethod
+    def forward(ctx, x):
+        ctx.n = x.shape[-1]
+        return _run_real(x, ctx.n, FORWARD)
+
+    @staticmethod
+    def backward(ctx, g):
+        n = ctx.n
+        G = g.contiguous().clone()
+        G[..., 1:n // 2] *= 0.5
+        return _run_real(G, n, INVERSE) * n
+
+
+class _IRFFT(torch.autograd.Function):
+    """x = irfft(X, n).  The gradient is rfft(g) / n with the interior bins
+    doubled (each stands for itself and its conjugate partner)."""
+
+    @staticmethod
+    def forward(ctx, X, n):
+        ctx.n = n
+        return _run_real(X, n, INVERSE)
+
+    @staticmethod
+    def backward(ctx, g):
+        n = ctx.n
+        R = _run_real(g.contiguous(), n, FORWARD)
+        R[..., 1:n // 2] *= 2.0
+        return R / n, None
+
+
+def rfft(x: torch.Tensor) -> torch.Tensor:
+    """Eq. 1 of real rows (last dimension, length n a power of two >= 4):
+    the n/2 + 1 non-redundant outputs.  x: float32 CUDA tensor; returns
+    complex64.  One fused kernel for n <= 2^15.  Differentiable."""
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.float32 or not x.is_cuda:
+        raise TypeError("expected a float32 CUDA tensor")
+    return _RFFT.apply(x.contiguous())
+
+
+def irfft(X: torch.Tensor, n: int | None = None) -> torch.Tensor:
+    """Eq. 2 (with 1/n) of the Hermitian extension of X[0..n/2] (last
+    dimension): real rows of length n (default 2 * (X.shape[-1] - 1)); the
+    imaginary parts of X[0] and X[n/2] are ignored.  Differentiable."""
+    _check_input(X)
+    if n is None:
+        n = 2 * (X.shape[-1] - 1)
+    if X.shape[-1] != n // 2 + 1:
+        raise ValueError(f"irfft: {X.shape[-1]} values for length {n}")
+    return _IRFFT.apply(X.contiguous(), int(n))
 
 
 class HostPipeline:

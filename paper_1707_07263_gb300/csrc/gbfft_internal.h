@@ -28,10 +28,14 @@ struct PassDesc {
 };
 constexpr int kMaxPasses = 4;
 
-enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3 };
+enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3, KIND_REAL = 4 };
 
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false);
 cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);
+cudaError_t launch_r2c_split(const float2* z, float2* x, long long M, long long batch, const float2* lo,
+                             const float2* hi, int s, cudaStream_t st);
+cudaError_t launch_c2r_split(const float2* x, float2* z, long long M, long long batch, const float2* lo,
+                             const float2* hi, int s, cudaStream_t st);
 
 }  // namespace gbfft
 
@@ -56,6 +60,18 @@ struct fft_plan {
   const gbfft::TileKernelInfo* krc;   // fused range-compression kernel of the length (or NULL)
   void* d_rctw;                       // its remainder-last stage table (NULL: the length's own table)
   long long rc_grid;                  // its grid when persistent (0: one tile per CTA)
+
+  // real-data plans (KIND_REAL, n = N reals, M = N/2): fused kernels for
+  // M <= 2^14, else the complex length-M plan `inner` plus the split kernels
+  // through `zbuf` (batch*M complex values after the inner workspace)
+  const gbfft::TileKernelInfo* kr2c;
+  const gbfft::TileKernelInfo* kc2r;
+  fft_plan* inner;
+  void* d_rtw;        // W_N^k, k < M, two-level: r_lo[k & (2^r_s - 1)] * r_hi[k >> r_s]
+  const float2* r_lo;
+  const float2* r_hi;
+  int r_s;
+  float2* zbuf;
   const float2* pre_tw;               // its W_N^n table, n < N/2
   long long tma_grid;                 // its resident-CTA grid
 

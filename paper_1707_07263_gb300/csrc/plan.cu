@@ -163,6 +163,8 @@ static fft_plan* new_plan() {
 
 static void free_plan(fft_plan* p) {
   if (!p) return;
+  if (p->inner) free_plan(p->inner);
+  if (p->d_rtw) cudaFree(p->d_rtw);
   if (p->many) many_plan_free(p);
   if (p->fused) fused_plan_free(p);
   if (p->ws_owned && p->ws) cudaFree(p->ws);
@@ -394,6 +396,54 @@ static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const fl
   return FFT_OK;
 }
 
+int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s);
+
+// ---- real-data transforms (KIND_REAL): N = 2M reals per row ----------------
+static int exec_real(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
+  if (dir != FFT_FORWARD && dir != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
+  if ((const void*)in == (const void*)out) return FFT_ERR_INVALID_ARG;
+  const long long M = p->n / 2;
+  if (p->kr2c) {
+    const TileKernelInfo* k = dir == FFT_FORWARD ? p->kr2c : p->kc2r;
+    const int C = k->C;
+    TileArgs a;
+    base_args(a);
+    a.in = in;
+    a.out = out;
+    a.tw = p->tw1;
+    a.tiles_per_batch = (p->batch + C - 1) / C;
+    a.ncols = p->batch;
+    a.r_w = p->r_lo;   // one-level table W_N^k, k < M
+    a.in_sn = a.out_sn = 1;
+    if (dir == FFT_FORWARD) {
+      // rows of M complex (2M reals) in, rows of M + 1 complex out
+      a.in_gstride = (long long)C * M;
+      a.in_sc = M;
+      a.out_gstride = (long long)C * (M + 1);
+      a.out_sc = M + 1;
+    } else {
+      a.in_gstride = (long long)C * (M + 1);
+      a.in_sc = M + 1;
+      a.out_gstride = (long long)C * M;
+      a.out_sc = M;
+      a.conj_in = 1;
+      a.scale_out = 1;
+      a.sx = (float)(1.0 / (double)M);
+      a.sy = -a.sx;
+    }
+    return launch_tile(k, a, a.tiles_per_batch, s);
+  }
+  if (!p->inner || !p->zbuf) return FFT_ERR_NO_WORKSPACE;
+  if (dir == FFT_FORWARD) {
+    const int rc = exec_plan(p->inner, in, p->zbuf, FFT_FORWARD, s);
+    if (rc) return rc;
+    return launch_r2c_split(p->zbuf, out, M, p->batch, p->r_lo, p->r_hi, p->r_s, s) == cudaSuccess ? FFT_OK
+                                                                                                  : FFT_ERR_CUDA;
+  }
+  if (launch_c2r_split(in, p->zbuf, M, p->batch, p->r_lo, p->r_hi, p->r_s, s) != cudaSuccess) return FFT_ERR_CUDA;
+  return exec_plan(p->inner, p->zbuf, out, FFT_INVERSE, s);
+}
+
 int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
   if (!p || !in || !out || !valid_dir(dir)) return FFT_ERR_INVALID_ARG;
   if (((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return FFT_ERR_ALIGN;
@@ -416,6 +466,7 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
         break;
       case KIND_2D: rc = exec_passes(p, fin, fout, dir, s); break;
       case KIND_MANY: rc = many_exec(p, fin, fout, dir, s); break;
+      case KIND_REAL: rc = exec_real(p, fin, fout, dir, s); break;
       default: rc = FFT_ERR_INVALID_ARG;
     }
   }
@@ -887,6 +938,72 @@ fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec) {
   return create_1d(n, batch, dir, prec, nullptr);
 }
 
+static int plan_real(fft_plan* p, int lgN) {
+  const int lgM = lgN - 1;
+  const long long M = 1LL << lgM;
+  // W_N^k for k < M: one level (M entries) for the fused kernels, two levels
+  // (r_lo[k & (2^r_s - 1)] * r_hi[k >> r_s]) for the split kernels
+  p->r_s = lgM <= 14 ? lgM : (lgM + 1) / 2;
+  const long long nlo = 1LL << p->r_s, nhi = 1LL << (lgM - p->r_s);
+  const size_t hi_off = align256((size_t)nlo * 8);
+  if (cudaMalloc(&p->d_rtw, hi_off + (size_t)nhi * 8) != cudaSuccess) return FFT_ERR_ALLOC;
+  p->r_lo = (const float2*)p->d_rtw;
+  p->r_hi = (const float2*)((char*)p->d_rtw + hi_off);
+  if (launch_gen_power_twiddles((float2*)p->r_lo, lgN, nlo, 1, 0) != cudaSuccess ||
+      launch_gen_power_twiddles((float2*)p->r_hi, lgN, nhi, nlo, 0) != cudaSuccess ||
+      cudaStreamSynchronize(0) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  p->lg = p->lg1 = lgM;
+  if (lgM <= 14) {
+    p->kr2c = tile_kernel_r2c(lgM);
+    p->kc2r = tile_kernel_c2r(lgM);
+    if (!p->kr2c || !p->kc2r) return FFT_ERR_UNSUPPORTED;
+    int rc = prepare_kernel(p->kr2c);
+    if (!rc) rc = prepare_kernel(p->kc2r);
+    if (rc) return rc;
+    p->k1 = p->kr2c;
+    p->c1 = p->kr2c->C;
+    p->launches = 1;
+    return build_tables(p, lgM, 0, 0);
+  }
+  p->inner = create_1d(M, p->batch, FFT_FORWARD, FFT_PREC_FP32, nullptr);
+  if (!p->inner) return fft_last_error();
+  p->launches = p->inner->launches + 1;
+  p->lg2 = p->inner->lg2;
+  p->d_status = p->inner->d_status;
+  p->ws_bytes = align256(p->inner->ws_bytes) + (size_t)M * (size_t)p->batch * 8;
+  return FFT_OK;
+}
+
+fft_plan* fft_plan_create_r2c(int64_t n, int64_t batch, int prec) {
+  const int lgN = ilog2_exact(n);
+  if (lgN < 2 || lgN > FFT_MAX_LOG2N || batch < 1 || !valid_prec(prec) || (double)n * (double)batch > 9.0e15) {
+    set_err(FFT_ERR_INVALID_ARG);
+    return nullptr;
+  }
+  if (prec != FFT_PREC_FP32) {
+    set_err(FFT_ERR_UNSUPPORTED);
+    return nullptr;
+  }
+  fft_plan* p = new_plan();
+  if (!p) {
+    set_err(FFT_ERR_ALLOC);
+    return nullptr;
+  }
+  p->kind = KIND_REAL;
+  p->n = n;
+  p->batch = batch;
+  p->dir = FFT_FORWARD;
+  p->prec = prec;
+  const int rc = plan_real(p, lgN);
+  if (rc != FFT_OK) {
+    free_plan(p);
+    set_err(rc);
+    return nullptr;
+  }
+  return p;
+}
+
 fft_plan* fft_plan_create_config(int64_t n, int64_t batch, int dir, int prec, const fft_plan_config* cfg) {
   return create_1d(n, batch, dir, prec, cfg);
 }
@@ -1008,6 +1125,16 @@ void fft_destroy(fft_plan* plan) { free_plan(plan); }
 
 size_t fft_plan_workspace_bytes(const fft_plan* plan) { return plan ? plan->ws_bytes : 0; }
 
+// A real-data plan hands the front of its workspace to its complex plan and
+// keeps the rest for Z.
+static void distribute_real_ws(fft_plan* plan) {
+  if (plan->kind != KIND_REAL || !plan->inner) return;
+  char* base = (char*)plan->ws;
+  plan->inner->ws = (base && plan->inner->ws_bytes) ? base : nullptr;
+  plan->inner->ws_owned = 0;
+  plan->zbuf = base ? (float2*)(base + align256(plan->inner->ws_bytes)) : nullptr;
+}
+
 int fft_plan_set_workspace(fft_plan* plan, void* dev_ptr) {
   if (!plan) return set_err(FFT_ERR_INVALID_ARG);
   if (dev_ptr && ((uintptr_t)dev_ptr & 255)) return set_err(FFT_ERR_ALIGN);
@@ -1016,14 +1143,17 @@ int fft_plan_set_workspace(fft_plan* plan, void* dev_ptr) {
   plan->ws_owned = 0;
   if (dev_ptr) {
     plan->ws = dev_ptr;
+    distribute_real_ws(plan);
     return FFT_OK;
   }
   if (plan->ws_bytes == 0) return FFT_OK;
   if (cudaMalloc(&plan->ws, plan->ws_bytes) != cudaSuccess) {
     plan->ws = nullptr;
+    distribute_real_ws(plan);
     return set_err(FFT_ERR_ALLOC);
   }
   plan->ws_owned = 1;
+  distribute_real_ws(plan);
   return FFT_OK;
 }
 
@@ -1034,11 +1164,11 @@ int fft_plan_kind(const fft_plan* plan) { return plan ? plan->kind : -1; }
 
 int fft_plan_describe(const fft_plan* p, char* buf, size_t len) {
   if (!p || !buf || len == 0) return set_err(FFT_ERR_INVALID_ARG);
-  static const char* kinds[] = {"single", "fourstep", "2d", "many"};
+  static const char* kinds[] = {"single", "fourstep", "2d", "many", "real", "?", "?", "?"};
   snprintf(buf, len,
            "kind=%s n=%lld batch=%lld lg1=%d lg2=%d c1=%d c2=%d threads1=%d smem1=%d threads2=%d smem2=%d "
            "prec=%d launches=%d ws=%zu tma_grid=%lld",
-           kinds[p->kind & 3], (long long)p->n, (long long)p->batch, p->lg1, p->lg2, p->c1, p->c2,
+           kinds[p->kind & 7], (long long)p->n, (long long)p->batch, p->lg1, p->lg2, p->c1, p->c2,
            p->k1 ? p->k1->threads : 0, p->k1 ? p->k1->smem_bytes : 0, p->k2 ? p->k2->threads : 0,
            p->k2 ? p->k2->smem_bytes : 0, p->prec, p->launches, p->ws_bytes, p->ktma ? p->tma_grid : 0LL);
   return FFT_OK;

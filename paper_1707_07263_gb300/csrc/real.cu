@@ -1,0 +1,95 @@
+// real.cu -- the even/odd split of real-data transforms longer than one
+// on-chip pass (N = 2M reals, M > 2^14): the complex length-M plan runs on
+// the row read as z[m] = x[2m] + i x[2m+1], and these kernels turn Z into the
+// N/2 + 1 outputs of Eq. 1 (real-to-complex) or X into Z (complex-to-real).
+// Each thread handles the pair (k, M - k), so every value is read once.
+#include <cuda_runtime.h>
+
+#include "gbfft_internal.h"
+
+namespace gbfft {
+
+__device__ __forceinline__ float2 w_two_level(const float2* lo, const float2* hi, int s, long long k) {
+  return cmul(__ldg(lo + (k & ((1LL << s) - 1))), __ldg(hi + (k >> s)));
+}
+
+// X[k] = E + W_N^k O, E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / (2i),
+// for the pair k = q, M - q (q = 0..M/2; Z[M] = Z[0], W_N^M = -1).
+__global__ void r2c_split_kernel(const float2* __restrict__ z, float2* __restrict__ x, long long M, long long batch,
+                                 const float2* lo, const float2* hi, int s) {
+  const long long half = M / 2 + 1;
+  const long long total = half * batch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / half, q = i - b * half;
+    const float2* zr = z + b * M;
+    float2* xr = x + b * (M + 1);
+    const float2 zk = __ldcs(zr + q);
+    const float2 zm = __ldcs(zr + ((M - q) & (M - 1)));
+    const float2 w = w_two_level(lo, hi, s, q);
+    {
+      const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      __stcs(xr + q, cadd(e, cmul(w, o)));
+    }
+    if (M - q != q) {
+      // the partner output M - q: roles of zk and zm swap, W_N^{M-q} = -conj(W_N^q)
+      const float2 e = make_float2(0.5f * (zm.x + zk.x), 0.5f * (zm.y - zk.y));
+      const float2 o = make_float2(0.5f * (zm.y + zk.y), -0.5f * (zm.x - zk.x));
+      __stcs(xr + (M - q), cadd(e, cmul(make_float2(-w.x, w.y), o)));
+    }
+  }
+}
+
+// Z[k] = E + i O, E = (X[k] + conj X[M-k]) / 2, O = (X[k] - conj X[M-k]) W_N^{-k} / 2,
+// for the pair k = q, M - q (q = 0..M/2; M - q < M only); Im X[0], Im X[M] do not enter.
+__global__ void c2r_split_kernel(const float2* __restrict__ x, float2* __restrict__ z, long long M, long long batch,
+                                 const float2* lo, const float2* hi, int s) {
+  const long long half = M / 2 + 1;
+  const long long total = half * batch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / half, q = i - b * half;
+    const float2* xr = x + b * (M + 1);
+    float2* zr = z + b * M;
+    float2 xk = __ldcs(xr + q);
+    float2 xm = __ldcs(xr + (M - q));
+    if (q == 0) {
+      xk.y = 0.f;
+      xm.y = 0.f;
+    }
+    const float2 w = w_two_level(lo, hi, s, q);
+    {
+      const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y - xm.y));
+      const float2 d = make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y + xm.y));
+      const float2 o = cmul(d, make_float2(w.x, -w.y));
+      __stcs(zr + q, make_float2(e.x - o.y, e.y + o.x));
+    }
+    if (q != 0 && M - q != q) {
+      // Z[M - q]: W_N^{-(M-q)} = conj(-conj(W_N^q)) = -W_N^q
+      const float2 e = make_float2(0.5f * (xm.x + xk.x), 0.5f * (xm.y - xk.y));
+      const float2 d = make_float2(0.5f * (xm.x - xk.x), 0.5f * (xm.y + xk.y));
+      const float2 o = cmul(d, make_float2(-w.x, -w.y));
+      __stcs(zr + (M - q), make_float2(e.x - o.y, e.y + o.x));
+    }
+  }
+}
+
+static unsigned split_grid(long long total) {
+  long long g = (total + 255) / 256;
+  return (unsigned)(g < 152 * 16 ? (g < 1 ? 1 : g) : 152 * 16);
+}
+
+cudaError_t launch_r2c_split(const float2* z, float2* x, long long M, long long batch, const float2* lo,
+                             const float2* hi, int s, cudaStream_t st) {
+  r2c_split_kernel<<<split_grid((M / 2 + 1) * batch), 256, 0, st>>>(z, x, M, batch, lo, hi, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2r_split(const float2* x, float2* z, long long M, long long batch, const float2* lo,
+                             const float2* hi, int s, cudaStream_t st) {
+  c2r_split_kernel<<<split_grid((M / 2 + 1) * batch), 256, 0, st>>>(x, z, M, batch, lo, hi, s);
+  return cudaGetLastError();
+}
+
+}  // namespace gbfft

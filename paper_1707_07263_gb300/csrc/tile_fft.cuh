@@ -177,6 +177,9 @@ struct TileArgs {
   long long filt_mask;
   // Stage table of the remainder-last schedule (REV passes).
   const float2* tw_rev;
+  // Real-data transforms of length N = 2L (rows of L complex values = 2L
+  // reals): r_w[k] = W_N^k, k < L.
+  const float2* r_w;
 };
 
 template <int R>
@@ -206,9 +209,12 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 // barriers that separate it from its neighbours).
 //   PRE  0: first pass reads global memory; 1: two-CTA radix-2 split;
 //        2: first pass reads a TMA-staged box; 4: the first pass's inputs are
-//        already in registers (left there by a POST == 2 transform), no conj_in.
+//        already in registers (left there by a POST == 2 transform), no conj_in;
+//        5: first pass builds Z[n] = E[n] + i O[n] of a complex-to-real
+//        transform from X[n] and X[L - n] of rows of L + 1 values (C2R).
 //   POST 0: last pass stores to global memory; 2: last pass multiplies output
-//        k by filt[k] and conjugates it, in registers.
+//        k by filt[k] and conjugates it, in registers; 3: last pass leaves
+//        output k in shared memory at sidx(k) (natural order).
 //   REV: remainder-last radix schedule (tables from a.tw_rev).  A POST == 2
 //        transform (radix-16 last pass: thread j holds k = j + q*L/16) feeds a
 //        PRE == 4, REV transform (radix-16 first pass: thread j reads n = j +
@@ -253,7 +259,31 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       const long long isn = IN_CF ? a.in_sn : 1;
       const float2* p = (OFFS ? gin + (ok ? a.col_off[cc[i]] : 0) : gin + cc[i] * a.in_sc) + (long long)jj[i] * isn;
       const long long step = (long long)LR * isn;
-      if constexpr (PRE == 2) {
+      if constexpr (PRE == 5) {
+        // complex-to-real: E = (X[n] + conj X[L-n]) / 2,
+        // O = (X[n] - conj X[L-n]) W_N^{-n} / 2, Z = E + i O; Im X[0] and
+        // Im X[L] do not enter.  Rows hold L + 1 values (in_sc).  All loads
+        // are issued before any arithmetic.
+        float2 x1[R], x2[R], w[R];
+        const float2* pm = p + (long long)(L - 2 * jj[i]);   // X[L - n] = pm[-r * step]
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          x1[r] = ok ? __ldg(p + r * step) : make_float2(0.f, 0.f);
+          x2[r] = ok ? __ldg(pm - r * step) : make_float2(0.f, 0.f);
+          w[r] = __ldg(a.r_w + jj[i] + r * LR);
+        }
+        if (jj[i] == 0) {   // n == 0 only for r == 0
+          x1[0].y = 0.f;
+          x2[0].y = 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float2 e = make_float2(0.5f * (x1[r].x + x2[r].x), 0.5f * (x1[r].y - x2[r].y));
+          const float2 d = make_float2(0.5f * (x1[r].x - x2[r].x), 0.5f * (x1[r].y + x2[r].y));
+          const float2 o = cmul(d, make_float2(w[r].x, -w[r].y));
+          v[i * R + r] = make_float2(e.x - o.y, e.y + o.x);
+        }
+      } else if constexpr (PRE == 2) {
         // column tile already staged in shared memory by a tensor TMA copy,
         // laid out [n][c] (gin points at it)
 #pragma unroll
@@ -313,7 +343,46 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   for (int i = 0; i < NB; ++i) dft_fwd<R>(v + i * R);
 
   // ---- scatter outputs ----
-  if constexpr (LAST && POST == 2) {
+  if constexpr (LAST && POST == 3) {
+    // real-to-complex split: thread j holds Z[k], k = j + q*NS; the partner
+    // Z[L - k] of every one of them lives in thread NS - j (q' = R - 1 - q),
+    // or in thread 0 itself for j = 0, so one exchange gives each thread all
+    // it needs:  X[k] = E + W_N^k O,  E = (Z[k] + conj Z[L-k]) / 2,
+    //            O = (Z[k] - conj Z[L-k]) / (2i),  plus X[L] from Z[0].
+    static_assert(NB == 1 && IDX == 0 && !OUT_CF && !REV, "real split: contiguous rows");
+    const int c = cc[0], j = jj[0];
+    __syncthreads();   // all reads of this pass are done
+    float2* wp = sm + c * LP + pidx(j);
+#pragma unroll
+    for (int q = 0; q < R; ++q) wp[pidx_c(q * NS)] = v[q];
+    __syncthreads();
+    if ((col0 + c) < a.ncols) {
+      const float2* zr = sm + c * LP;
+      float2* orow = gout + c * a.out_sc;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int k = j + q * NS;
+        const float2 zk = v[q];
+        const float2 zm = zr[pidx((L - k) & (L - 1))];
+        const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        const float2 x = cadd(e, cmul(__ldg(a.r_w + k), o));
+        if (a.stream_out)
+          __stcs(orow + k, x);
+        else
+          __stcg(orow + k, x);
+      }
+      if (j == 0) {
+        // X[L] = E[0] - O[0] (W_N^L = -1)
+        const float2 z0 = v[0];
+        const float2 x = make_float2(z0.x - z0.y, 0.f);
+        if (a.stream_out)
+          __stcs(orow + L, x);
+        else
+          __stcg(orow + L, x);
+      }
+    }
+  } else if constexpr (LAST && POST == 2) {
     static_assert(NB == 1 && IDX == 0 && !OUT_CF && !REV, "fused filter pass: contiguous rows");
     // output k = j + q*NS stays in the thread as conj(filt[k] * X[k])
     const int j = jj[0];
@@ -558,6 +627,41 @@ __global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T, rc_min_blocks
     if constexpr (!rc_persistent(LG)) break;
     __syncthreads();   // the next tile's first exchange overwrites this one's
   }
+}
+
+// Real-to-complex transform of rows of N = 2L reals (Sec. 2.1's split of a
+// sequence into even and odd samples): the row read as L complex values
+// z[m] = x[2m] + i x[2m+1] is transformed on chip (Z = Eq. 1 of length L) and
+// the last pass turns Z into X[0..L] (POST == 3), written to rows of L + 1
+// complex values (out_sc).  One read and one write of every value.
+template <int LG, int C>
+__global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T) tile_r2c_kernel(const TileArgs a) {
+  extern __shared__ float2 smem[];
+  using Cfg = TileCfg<LG, C, false, false>;
+  const long long tile = blockIdx.x;
+  const long long b = tile / a.tiles_per_batch;
+  const long long g = tile - b * a.tiles_per_batch;
+  float2 v[Cfg::P];
+  tile_stage<LG, C, false, false, 0, false, 0, 3>(v, smem, a, a.in + b * a.in_bstride + g * a.in_gstride,
+                                                  a.out + b * a.out_bstride + g * a.out_gstride, g * C, b, nullptr);
+}
+
+// Complex-to-real transform (the inverse of tile_r2c_kernel): rows of L + 1
+// values X[0..L] (in_sc) become rows of N = 2L reals.  The first pass builds
+// Z[n] = E[n] + i O[n] from X[n] and X[L - n] (PRE == 5) and the tile runs
+// the inverse length-L transform by conjugation (conj_in = 1, a.sx = 1/L,
+// a.sy = -1/L); z[m] = x[2m] + i x[2m+1] is stored as L complex values.
+template <int LG, int C>
+__global__ void __launch_bounds__(TileCfg<LG, C, false, false>::T, rc_min_blocks(TileCfg<LG, C, false, false>::T))
+    tile_c2r_kernel(const TileArgs a) {
+  extern __shared__ float2 smem[];
+  using Cfg = TileCfg<LG, C, false, false>;
+  const long long tile = blockIdx.x;
+  const long long b = tile / a.tiles_per_batch;
+  const long long g = tile - b * a.tiles_per_batch;
+  float2 v[Cfg::P];
+  tile_stage<LG, C, false, false, 0, false, 5, 0>(v, smem, a, a.in + b * a.in_bstride + g * a.in_gstride,
+                                                  a.out + b * a.out_bstride + g * a.out_gstride, g * C, b, nullptr);
 }
 
 }  // namespace gbfft

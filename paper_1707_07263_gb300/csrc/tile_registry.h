@@ -40,6 +40,11 @@ const TileKernelInfo* tile_kernel_dif2(int lg);
 // lengths 2^12..2^14 (one transform per CTA); signature void(TileArgs, long long).
 const TileKernelInfo* tile_kernel_pf(int lg);
 
+// Fused real-to-complex / complex-to-real kernels for half length 2^lg
+// (N = 2^(lg+1) reals), 2^1..2^14, jj_cols(lg) rows per CTA.
+const TileKernelInfo* tile_kernel_r2c(int lg);
+const TileKernelInfo* tile_kernel_c2r(int lg);
+
 // Fused range-compression kernels (tile_rc_kernel), lengths 2^1..2^14 with
 // jj_cols(lg) rows per CTA.
 const TileKernelInfo* tile_kernel_rc(int lg);

@@ -79,6 +79,16 @@ def test_plan_create_many_rejects(lib):
     assert lib.fft_last_error() == -1
 
 
+def test_plan_create_r2c_rejects(lib):
+    assert lib.fft_plan_create_r2c(12, 1, 0) is None      # not a power of two
+    assert lib.fft_plan_create_r2c(2, 1, 0) is None       # below 4
+    assert lib.fft_plan_create_r2c(1 << 29, 1, 0) is None  # above 2^28
+    assert lib.fft_plan_create_r2c(16, 0, 0) is None
+    assert lib.fft_last_error() == -1
+    assert lib.fft_plan_create_r2c(16, 1, 1) is None      # tensor-core precisions: not for real data
+    assert lib.fft_last_error() == -6
+
+
 def test_null_plan_calls(lib):
     assert lib.fft_exec(None, None, None, None) == -1
     assert lib.fft_exec_dir(None, None, None, 0, None) == -1
@@ -98,3 +108,7 @@ def test_python_api_fails_loudly_without_cuda_tensor():
         gb.fft(torch.zeros(16, dtype=torch.complex64))   # CPU tensor: no fallback
     with pytest.raises(TypeError):
         gb.range_compress(torch.zeros(16, dtype=torch.complex64), torch.zeros(16, dtype=torch.complex64))
+    with pytest.raises(TypeError):
+        gb.rfft(torch.zeros(16, dtype=torch.float32))
+    with pytest.raises(TypeError):
+        gb.irfft(torch.zeros(9, dtype=torch.complex64))
