@@ -9,14 +9,18 @@
 //   kind 1  four-step column tile (C columns of length N1, with the W_N^{n2*k1}
 //           twiddle) of a transform with 2^13 <= N <= 2^16;
 //   kind 2  four-step row tile of such a transform, written transposed.
-// Queue order: every kind-1 tile (largest transforms first), then the batch
-// tiles (largest first), then every kind-2 tile.  CTAs pop items with one
-// atomicAdd on a queue head, claiming the next item while working on the
-// current one.  A kind-2 tile waits until all kind-1 tiles of
-// its transform have been written (a per-transform completion counter); since
-// those were dequeued earlier by CTAs that never wait, the wait always ends --
-// it is still bounded (clock64 budget) and a timeout sets FFT_ERR_TIMEOUT in
-// the plan's status word instead of hanging.  The queue head and counters are
+// Queue order: the kind-1 tiles of the four-step transforms (largest first),
+// each transform's kind-2 tiles following its kind-1 tiles once about two
+// grids' worth of further items have been queued, then the batch tiles
+// (largest first).  The distance lets the column tiles finish before their row
+// tiles are dequeued, and keeps the intermediate of the transforms in flight
+// (~two grids of 4096-point tiles, ~30 MB) in L2 between the two passes.
+// CTAs pop items with one atomicAdd on a queue head, claiming the next item
+// while working on the current one.  A kind-2 tile waits until all kind-1
+// tiles of its transform have been written (a per-transform completion
+// counter); since those were dequeued earlier by CTAs that never wait, the
+// wait always ends -- it is still bounded (clock64 budget) and a timeout sets
+// FFT_ERR_TIMEOUT in the plan's status word instead of hanging.  The queue head and counters are
 // cleared by a memset issued with every exec, so exec can be captured into a
 // CUDA graph and replayed.
 #include <cuda_runtime.h>
@@ -177,7 +181,7 @@ __device__ __forceinline__ void many_row_tile(const ManyArgs& m, const ManyItem&
   tile_body<LG2, C, false, true>(a, it.g, smem);
 }
 
-__global__ void __launch_bounds__(kManyThreads, 3) many_kernel(const ManyArgs m) {
+__global__ void __launch_bounds__(kManyThreads, 4) many_kernel(const ManyArgs m) {
   extern __shared__ float2 smem[];
   __shared__ int s_next;
   __shared__ long long s_off[256];
@@ -259,7 +263,7 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
     }
   }
   // batch tiles: group transforms of equal length (<= 2^12), largest first
-  std::vector<ManyItem> col_items, batch_items, row_items;
+  std::vector<ManyItem> batch_items;
   std::vector<long long> slots;
   std::vector<ManyTransform> trs;
   long long ws_total = 0;
@@ -278,7 +282,26 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
       batch_items.push_back(it);
     }
   }
-  // four-step transforms, largest first
+  // resident CTAs of the persistent launch (sets the queue distance below)
+  if (cudaFuncSetAttribute(many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kManySmem) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, many_kernel, kManyThreads, kManySmem) != cudaSuccess ||
+      per_sm < 1)
+    return FFT_ERR_CUDA;
+  const size_t resident = (size_t)per_sm * (size_t)sms;
+  // items queued between a transform's column and row tiles (in units of
+  // half the resident grid; GBFFT_MANY_GAP overrides the default of 4)
+  const char* gap_env = getenv("GBFFT_MANY_GAP");
+  const size_t gap = (size_t)std::max(1, gap_env ? atoi(gap_env) : 4) * resident / 2;
+
+  // four-step transforms, largest first: column tiles in order, each
+  // transform's row tiles once `gap` more items have been queued
+  std::vector<ManyItem> fourstep;
+  std::vector<std::pair<size_t, size_t>> pending;   // (queue position of the last column tile, transform)
+  std::vector<std::vector<ManyItem>> rows_of;
   for (int L = 16; L >= 13; --L) {
     for (int64_t i = 0; i < count; ++i) {
       if (lg[i] != L) continue;
@@ -294,16 +317,24 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
       const int tr = (int)trs.size();
       const int ncol_tiles = (int)((1LL << t.lg2) / t.c1);
       const int nrow_tiles = (int)((1LL << t.lg1) / t.c2);
-      for (int g = 0; g < ncol_tiles; ++g) col_items.push_back(ManyItem{1, t.lg1, t.c1, tr, g, 0});
-      for (int g = 0; g < nrow_tiles; ++g) row_items.push_back(ManyItem{2, t.lg2, t.c2, tr, g, ncol_tiles});
+      for (int g = 0; g < ncol_tiles; ++g) fourstep.push_back(ManyItem{1, t.lg1, t.c1, tr, g, 0});
+      rows_of.emplace_back();
+      for (int g = 0; g < nrow_tiles; ++g) rows_of.back().push_back(ManyItem{2, t.lg2, t.c2, tr, g, ncol_tiles});
+      pending.emplace_back(fourstep.size(), (size_t)tr);
       trs.push_back(t);
+      // release the row tiles of every transform whose column tiles are far enough back
+      size_t k = 0;
+      while (k < pending.size() && fourstep.size() - pending[k].first >= gap) ++k;
+      for (size_t i = 0; i < k; ++i)
+        fourstep.insert(fourstep.end(), rows_of[pending[i].second].begin(), rows_of[pending[i].second].end());
+      pending.erase(pending.begin(), pending.begin() + k);
     }
   }
+  for (auto& pr : pending) fourstep.insert(fourstep.end(), rows_of[pr.second].begin(), rows_of[pr.second].end());
   std::vector<ManyItem> items;
-  items.insert(items.end(), col_items.begin(), col_items.end());
+  items.insert(items.end(), fourstep.begin(), fourstep.end());
   items.insert(items.end(), batch_items.begin(), batch_items.end());
-  items.insert(items.end(), row_items.begin(), row_items.end());
-  if (getenv("GBFFT_TEST_MISSING_PRODUCER") && atoi(getenv("GBFFT_TEST_MISSING_PRODUCER")) && !row_items.empty()) {
+  if (getenv("GBFFT_TEST_MISSING_PRODUCER") && atoi(getenv("GBFFT_TEST_MISSING_PRODUCER")) && !trs.empty()) {
     // test hook: one row tile waits for a column tile that does not exist
     for (ManyItem& it : items)
       if (it.kind == 2) {
@@ -371,15 +402,7 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
   if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return FFT_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return FFT_ERR_CUDA;
 
-  if (cudaFuncSetAttribute(many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kManySmem) != cudaSuccess)
-    return FFT_ERR_CUDA;
-  int per_sm = 0, sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, many_kernel, kManyThreads, kManySmem) != cudaSuccess ||
-      per_sm < 1)
-    return FFT_ERR_CUDA;
-  mp->grid = (int)std::min<long long>((long long)per_sm * sms, (long long)items.size());
+  mp->grid = (int)std::min<long long>((long long)resident, (long long)items.size());
   mp->nitems = (int)items.size();
   mp->total = total;
   mp->d_counters = d_cnt;
