@@ -138,10 +138,11 @@ def fft2(x, dir: int = FORWARD, lib=None) -> np.ndarray:
 
 
 def transform(x, dir: int = FORWARD, lib=None) -> np.ndarray:
-    """The oracle's default route: the O(N^2) sum for N <= 1024, the radix-2
-    recursion above that."""
+    """The oracle's default route: the O(N^2) sum for N <= 1024 and for every
+    N that is not a power of two (Eq. 1 holds for any N), the radix-2
+    recursion for powers of two above 1024."""
     n = np.asarray(x).shape[-1]
-    return dft(x, dir, lib) if n <= 1024 else fft(x, dir, lib)
+    return dft(x, dir, lib) if (n <= 1024 or n & (n - 1)) else fft(x, dir, lib)
 
 
 def range_compress(x, H, lib=None) -> np.ndarray:

@@ -268,5 +268,23 @@ def check_real_transforms(lib, rf=None, irf=None):
         _close(irf(X, n), np.fft.irfft(X, n, axis=-1), 1e-12, f"irfft vs numpy N={n}")
 
 
+def check_mixed_lengths(lib):
+    """Lengths that are not powers of two (products of 2, 3, 5, 7) through the
+    default route: numpy's pocketfft, the delayed-delta closed form
+    (delta[n - n0] -> W_N^{k n0}), Parseval and the round trip."""
+    for n in (3, 5, 6, 7, 12, 15, 35, 100, 360, 1000):
+        x = _cvec(n, seed=1000 + n, batch=2)
+        _close(oracle.transform(x, oracle.FORWARD, lib=lib), np.fft.fft(x, axis=-1), 1e-12, f"mixed N={n} vs numpy")
+        X = oracle.transform(x, oracle.FORWARD, lib=lib)
+        _close(oracle.transform(X, oracle.INVERSE, lib=lib), x, 1e-12, f"mixed N={n} round trip")
+        assert abs(np.sum(np.abs(X) ** 2) - n * np.sum(np.abs(x) ** 2)) <= 1e-10 * n * np.sum(np.abs(x) ** 2)
+        n0 = n // 3 + 1
+        d = np.zeros(n, complex)
+        d[n0] = 1
+        k = np.arange(n)
+        _close(oracle.transform(d, lib=lib), np.exp(-2j * np.pi * ((k * n0) % n) / n), 1e-12, f"mixed N={n} delta")
+
+
 ALL_CHECKS = (check_golden, check_small_by_hand, check_closed_forms, check_invariants,
-              check_dft_vs_fft, check_numpy, check_fft2, check_range_compress, check_real_transforms)
+              check_dft_vs_fft, check_numpy, check_fft2, check_range_compress, check_real_transforms,
+              check_mixed_lengths)
