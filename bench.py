@@ -23,7 +23,7 @@ Also printed on the same JSON line:
 
 ``--impl reference`` times the oracle instead (the deliberately slow CPU
 baseline) and prints the same line with "impl": "reference".
-Other workloads for measurement only: --workload large | tc | many | range | real.
+Other workloads for measurement only: --workload large | tc | many | range | real | mixed.
 """
 from __future__ import annotations
 
@@ -845,6 +845,33 @@ def run_measure(args):
             del p
         desc = ("real-data transforms: 2^26 U[-1,1] reals per launch in rows of N; rfft -> N/2+1 complex, irfft "
                 "back; GFLOP/s counts 2.5 N log2 N per real row; cufft_torch = torch.fft.rfft (context)")
+    elif args.workload == "mixed":
+        # lengths that are not powers of two: ~2^26 points per launch
+        for n in (1000, 3000, 5000, 6000, 10000, 12000):
+            batch = TOTAL // n
+            x = torch.from_numpy(workloads.cgauss(n, batch, seed=workloads.seed_for(8) + n).reshape(-1)).to(dev)
+            y = torch.empty_like(x)
+            h, wsb = plan(n, batch, 0)
+            us = _time_fn(torch, lambda: run_plan(h, x, y), args.steps, args.warmup, stream) * 1e3
+
+            def cufft():
+                with torch.cuda.stream(stream):
+                    torch.fft.fft(x.view(batch, n))
+
+            cu = _time_fn(torch, cufft, args.steps, args.warmup, stream) * 1e3
+            run_plan(h, x, y)
+            torch.cuda.synchronize()
+            rows = [0, batch - 1]
+            xr = x.view(batch, n)[rows].cpu().numpy()
+            err = float(oracle.rel_l2_rows(y.view(batch, n)[rows].cpu().numpy(),
+                                           oracle.transform(xr.astype(np.complex128))).max())
+            res.append({"n": n, "batch": batch, "us": round(us, 1), "cufft_torch_us": round(cu, 1),
+                        "gflops": round(5.0 * n * np.log2(n) * batch / (us * 1e-6) / 1e9, 1),
+                        "hbm_frac": round(16.0 * n * batch / (us * 1e-6) / 1e9 / peak, 4),
+                        "err_sampled": float(f"{err:.3e}")})
+            lib.fft_destroy(h)
+        desc = ("mixed-radix lengths (2^a 3^b 5^c 7^d, one on-chip pass): ~2^26 CN(0,1) points per launch; "
+                "cufft_torch = torch.fft (context)")
     print(json.dumps({"workload": args.workload, "desc": desc, "results": res,
                       "peak_hbm_gbs": peak}), flush=True)
 
@@ -855,7 +882,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range", "real"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range", "real", "mixed"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

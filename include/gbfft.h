@@ -60,7 +60,7 @@ enum {
 
 enum {
   FFT_OK = 0,
-  FFT_ERR_INVALID_ARG = -1,   /* n not a power of two, n < 2, n too large, batch < 1, bad dir/prec, NULL */
+  FFT_ERR_INVALID_ARG = -1,   /* n not a supported length, batch < 1, bad dir/prec, NULL */
   FFT_ERR_ALIGN = -2,         /* data pointer not 8-byte aligned */
   FFT_ERR_NO_WORKSPACE = -3,  /* plan needs a workspace and none was set */
   FFT_ERR_CUDA = -4,          /* a CUDA runtime call or launch failed */
@@ -73,12 +73,17 @@ enum {
 #define FFT_MAX_LOG2N 28
 #define FFT_MAX_LOG2_SIDE 14
 
-/* Plan for `batch` 1-D transforms of length n (power of two, 2 <= n <= 2^28).
+/* Plan for `batch` 1-D transforms of length n: a power of two, 2 <= n <= 2^28,
+ * or (FP32 only) a product n = 2^a 3^b 5^c 7^d with 3 <= n <= 14336 (mixed
+ * radix: Eq. 1 holds for any n and the Cooley-Tukey split of Sec. 2.1 for
+ * any factorisation; one on-chip pass of radix-16/8/4/2/3/5/7 stages; a
+ * config must be NULL).
  * dir is the direction fft_exec uses (FFT_FORWARD, FFT_INVERSE, optionally
  * with FFT_ADJOINT); prec one of FFT_PREC_*.  Lengths up to 2^14 run as one
- * on-chip pass per transform (Sec. 2.3.2, "no need to divide"); longer ones
- * are split N = N1*N2 into a column pass with twiddle scaling and a row pass
- * through global memory (Sec. 2.3.2, "two times exchange").
+ * on-chip pass per transform (Sec. 2.3.2: short data is not partitioned);
+ * longer ones are split N = N1*N2 into a column pass with twiddle scaling and
+ * a row pass through global memory (Sec. 2.3.2: two exchanges between shared
+ * and global memory).
  * Builds the twiddle tables on the current device (FP64 sincospi rounded
  * once to FP32; Sec. 2.3.1 look-up table).  Returns NULL on error. */
 GBFFT_API fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec);
@@ -211,7 +216,7 @@ GBFFT_API int64_t fft_plan_batch(const fft_plan* plan);
 /* Number of kernel launches one fft_exec issues. */
 GBFFT_API int fft_plan_launches(const fft_plan* plan);
 /* Kind: 0 single on-chip pass, 1 four-step, 2 two-dimensional, 3 uneven batch,
- * 4 real data. */
+ * 4 real data, 5 mixed radix. */
 GBFFT_API int fft_plan_kind(const fft_plan* plan);
 /* Human-readable plan summary into buf (NUL-terminated); returns FFT_OK. */
 GBFFT_API int fft_plan_describe(const fft_plan* plan, char* buf, size_t len);

@@ -1,7 +1,7 @@
 // fused.cu -- the two passes of the four-step split in ONE persistent launch,
 // with the intermediate kept in L2.
 //
-// The paper's "two times exchange" (Sec. 2.3.2) writes the intermediate to
+// The paper's two-exchange scheme (Sec. 2.3.2) writes the intermediate to
 // global memory after the first pass and reads it back in the second, so a
 // two-pass transform moves every point through DRAM twice.  Here the batch is
 // cut into slabs of whole transforms (about 16 MB each) and the passes are

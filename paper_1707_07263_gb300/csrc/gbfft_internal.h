@@ -28,7 +28,27 @@ struct PassDesc {
 };
 constexpr int kMaxPasses = 4;
 
-enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3, KIND_REAL = 4 };
+enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3, KIND_REAL = 4, KIND_MIXED = 5 };
+
+// Lengths N = 2^a 3^b 5^c 7^d that are not powers of two (mixed.cu).
+constexpr int kMixedMaxPasses = 16;
+constexpr long long kMixedMaxN = 14336;   // two shared-memory buffers of N complex values fit
+struct MixedArgs {
+  const float2* in;
+  float2* out;
+  const float2* tw;   // W_N^m, m < N
+  int N, C;           // length; transforms per CTA
+  long long batch;
+  int nrad;
+  int rad[kMixedMaxPasses];
+  int conj_in, scale_out;
+  float sx, sy;
+};
+int mixed_radices(long long N, int* rad);
+int mixed_plan_init(fft_plan* p);
+int mixed_exec(fft_plan* p, const float2* in, float2* out, int conj, float sx, float sy, int scale_out,
+               cudaStream_t s);
+cudaError_t launch_gen_twiddles_n(float2* tab, long long N, long long count, cudaStream_t s);
 
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false);
 cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);
@@ -72,6 +92,10 @@ struct fft_plan {
   const float2* r_hi;
   int r_s;
   float2* zbuf;
+
+  // mixed-radix plans (KIND_MIXED)
+  gbfft::MixedArgs mixed;
+  int mixed_threads, mixed_smem;
   const float2* pre_tw;               // its W_N^n table, n < N/2
   long long tma_grid;                 // its resident-CTA grid
 

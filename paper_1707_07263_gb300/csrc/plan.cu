@@ -4,7 +4,7 @@
 //   * n <= 2^14: one on-chip pass per transform (paper Sec. 2.3.2: small data
 //     need no division; here the bound is GB300's shared memory and register
 //     file rather than the C2070's).
-//   * n  > 2^14: four-step split N = N1*N2 (Sec. 2.3.2 "two times exchange"):
+//   * n  > 2^14: four-step split N = N1*N2 (Sec. 2.3.2, two exchanges through global memory):
 //       pass 1  column FFTs of length N1 over stride N2, each output scaled by
 //               W_N^{n2*k1}, written to the workspace as Y[k1][n2];
 //       pass 2  row FFTs of length N2 of Y[k1][.], written transposed to
@@ -467,6 +467,12 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
       case KIND_2D: rc = exec_passes(p, fin, fout, dir, s); break;
       case KIND_MANY: rc = many_exec(p, fin, fout, dir, s); break;
       case KIND_REAL: rc = exec_real(p, fin, fout, dir, s); break;
+      case KIND_MIXED: {
+        const DirXf x = dir_xf(dir, p->n);
+        rc = mixed_exec(p, fin, fout, x.conj, x.scale, x.conj ? -x.scale : x.scale,
+                        (x.conj || x.scale != 1.0f) ? 1 : 0, s);
+        break;
+      }
       default: rc = FFT_ERR_INVALID_ARG;
     }
   }
@@ -905,8 +911,40 @@ static int build_2d(fft_plan* p, int ly, int lx) {
 // ============================================================================
 extern "C" {
 
+// Lengths that are not powers of two: 7-smooth N <= kMixedMaxN, one pass.
+static fft_plan* create_mixed(int64_t n, int64_t batch, int dir, int prec) {
+  int rad[kMixedMaxPasses];
+  if (n < 3 || n > kMixedMaxN || batch < 1 || !valid_dir(dir) || !valid_prec(prec) || mixed_radices(n, rad) == 0 ||
+      (double)n * (double)batch > 9.0e15) {
+    set_err(FFT_ERR_INVALID_ARG);
+    return nullptr;
+  }
+  if (prec != FFT_PREC_FP32) {
+    set_err(FFT_ERR_UNSUPPORTED);
+    return nullptr;
+  }
+  fft_plan* p = new_plan();
+  if (!p) {
+    set_err(FFT_ERR_ALLOC);
+    return nullptr;
+  }
+  p->kind = KIND_MIXED;
+  p->n = n;
+  p->batch = batch;
+  p->dir = dir;
+  p->prec = prec;
+  const int rc = mixed_plan_init(p);
+  if (rc != FFT_OK) {
+    free_plan(p);
+    set_err(rc);
+    return nullptr;
+  }
+  return p;
+}
+
 static fft_plan* create_1d(int64_t n, int64_t batch, int dir, int prec, const fft_plan_config* cfg) {
   const int lgN = ilog2_exact(n);
+  if (lgN < 0 && n > 2 && !cfg) return create_mixed(n, batch, dir, prec);
   if (lgN < 1 || lgN > FFT_MAX_LOG2N || batch < 1 || !valid_dir(dir) || !valid_prec(prec)) {
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
@@ -1164,7 +1202,7 @@ int fft_plan_kind(const fft_plan* plan) { return plan ? plan->kind : -1; }
 
 int fft_plan_describe(const fft_plan* p, char* buf, size_t len) {
   if (!p || !buf || len == 0) return set_err(FFT_ERR_INVALID_ARG);
-  static const char* kinds[] = {"single", "fourstep", "2d", "many", "real", "?", "?", "?"};
+  static const char* kinds[] = {"single", "fourstep", "2d", "many", "real", "mixed", "?", "?"};
   snprintf(buf, len,
            "kind=%s n=%lld batch=%lld lg1=%d lg2=%d c1=%d c2=%d threads1=%d smem1=%d threads2=%d smem2=%d "
            "prec=%d launches=%d ws=%zu tma_grid=%lld",

@@ -25,7 +25,7 @@
 //           transform -- coalesced when a transform's points are contiguous.
 //   c-fast: consecutive lanes take the same j of adjacent transforms c --
 //           coalesced when the C transforms are adjacent columns (the
-//           paper's "first dimension is 16" column pass, Sec. 2.3.2).
+//           paper's column pass over 16-wide groups, Sec. 2.3.2).
 // IN_CF / OUT_CF select c-fast for the global-facing first / last pass.
 //
 // Direction (Eq. 2, Eq. 4): the kernels always apply the forward W_N; the

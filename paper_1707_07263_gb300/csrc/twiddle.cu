@@ -42,6 +42,20 @@ __global__ void gen_power_twiddles(float2* tab, int lgN, long long count, long l
     tab[i] = w_entry((i * step) % N, N);
 }
 
+// tab[m] = W_N^m, m < count, for any N (mixed-radix lengths).
+__global__ void gen_twiddles_n(float2* tab, long long N, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    tab[i] = w_entry(i % N, N);
+}
+
+cudaError_t launch_gen_twiddles_n(float2* tab, long long N, long long count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const long long blocks = (count + 255) / 256;
+  gen_twiddles_n<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(tab, N, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev) {
   const int total = stage_tw_size(lg, rev);
   if (total == 0) return cudaSuccess;

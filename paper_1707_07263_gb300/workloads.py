@@ -1,6 +1,6 @@
 """Seeded synthetic inputs shaped like the paper's remote-sensing (SAR) FFT
-workloads (Sec. 3 names SAR imaging with transform lengths from a few
-thousand to tens of thousands of points).
+workloads (Sec. 3: SAR imaging, transforms of roughly 10^3 to a few 10^4
+points).
 
 This module only draws random numbers; it holds none of the transform's
 arithmetic.  Both the CUDA path's tests/benchmark and the FP64 oracle take

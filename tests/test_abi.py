@@ -48,7 +48,9 @@ def test_error_strings(lib):
 
 
 @pytest.mark.parametrize("n,batch,dir,prec", [
-    (12, 1, 0, 0),        # not a power of two
+    (11, 1, 0, 0),        # a prime factor above 7
+    (2 * 3 * 7 * 11, 1, 0, 0),
+    (3 << 13, 1, 0, 0),   # 7-smooth but beyond the one-pass mixed-radix limit (14336)
     (0, 1, 0, 0),
     (1, 1, 0, 0),         # N=1 is not supported
     (-8, 1, 0, 0),
@@ -62,6 +64,11 @@ def test_error_strings(lib):
 def test_plan_create_rejects(lib, n, batch, dir, prec):
     assert lib.fft_plan_create(n, batch, dir, prec) is None
     assert lib.fft_last_error() == -1
+
+
+def test_mixed_radix_tensor_core_is_unsupported(lib):
+    assert lib.fft_plan_create(12, 1, 0, 1) is None
+    assert lib.fft_last_error() == -6
 
 
 def test_plan_create_2d_rejects(lib):
