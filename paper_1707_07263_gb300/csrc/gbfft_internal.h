@@ -41,6 +41,10 @@ struct MixedArgs {
   long long batch;
   int nrad;
   int rad[kMixedMaxPasses];
+  // per pass: N/R and Ns with their reciprocals ceil(2^32 / d) (0 for d = 1):
+  // q = umulhi(n, m) is exact for n * d < 2^32, which every index here meets
+  unsigned nb[kMixedMaxPasses], nb_m[kMixedMaxPasses];
+  unsigned ns[kMixedMaxPasses], ns_m[kMixedMaxPasses];
   int conj_in, scale_out;
   float sx, sy;
 };

@@ -78,17 +78,20 @@ __device__ __forceinline__ void dft_any(float2* v) {
     dft_fwd<R>(v);
 }
 
-// One pass over the tile: C transforms of length N at src (global when
+// n / d from the reciprocal m = ceil(2^32 / d) (m = 0 stands for d = 1)
+__device__ __forceinline__ unsigned fdiv(unsigned n, unsigned m) { return m ? __umulhi(n, m) : n; }
+
+// One pass s over the tile: C transforms of length N at src (global when
 // FIRST, else shared memory), written to dst (global when LAST).
 template <int R>
-__device__ __forceinline__ void mixed_pass(const MixedArgs& a, const float2* src, float2* dst, bool first,
-                                           bool last, int Ns, long long col0) {
+__device__ __forceinline__ void mixed_pass(const MixedArgs& a, int s, const float2* src, float2* dst, bool first,
+                                           bool last, long long col0) {
   const int N = a.N;
-  const int NB = N / R;
-  const int total = a.C * NB;
-  const int stride = N / (Ns * R);
+  const unsigned NB = a.nb[s], nbm = a.nb_m[s], Ns = a.ns[s], nsm = a.ns_m[s];
+  const int total = a.C * (int)NB;
+  const int stride = N / ((int)Ns * R);
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
-    const int c = b / NB, j = b - c * NB;
+    const int c = (int)fdiv((unsigned)b, nbm), j = b - c * (int)NB;
     const bool ok = col0 + c < a.batch;
     float2 v[R];
     const float2* s = src + (long long)c * N + j;
@@ -103,13 +106,14 @@ __device__ __forceinline__ void mixed_pass(const MixedArgs& a, const float2* src
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
     }
-    const int k = j % Ns;
+    const int jq = (int)fdiv((unsigned)j, nsm);
+    const int k = j - jq * (int)Ns;
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(a.tw + r * k * stride));
     }
     dft_any<R>(v);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = jq * (int)Ns * R + k;
     float2* d = dst + (long long)c * N + base;
     if (last) {
       if (!ok) continue;
@@ -126,34 +130,37 @@ __device__ __forceinline__ void mixed_pass(const MixedArgs& a, const float2* src
   }
 }
 
-__global__ void __launch_bounds__(512) mixed_kernel(const MixedArgs a) {
+__global__ void __launch_bounds__(512, 2) mixed_kernel(const MixedArgs a) {
   extern __shared__ float2 smem[];
   const long long tile = blockIdx.x;
   const long long col0 = tile * a.C;
   const long long off = col0 * a.N;
-  float2* buf[2] = {smem, smem + (size_t)a.C * a.N};
-  int Ns = 1;
+  float2* const buf1 = smem + (size_t)a.C * a.N;
   for (int s = 0; s < a.nrad; ++s) {
     const bool first = s == 0, last = s == a.nrad - 1;
-    const float2* src = first ? a.in + off : buf[(s + 1) & 1];
-    float2* dst = last ? a.out + off : buf[s & 1];
+    const float2* src = first ? a.in + off : ((s & 1) ? smem : buf1);
+    float2* dst = last ? a.out + off : ((s & 1) ? buf1 : smem);
     switch (a.rad[s]) {
-      case 2: mixed_pass<2>(a, src, dst, first, last, Ns, col0); break;
-      case 3: mixed_pass<3>(a, src, dst, first, last, Ns, col0); break;
-      case 4: mixed_pass<4>(a, src, dst, first, last, Ns, col0); break;
-      case 5: mixed_pass<5>(a, src, dst, first, last, Ns, col0); break;
-      case 7: mixed_pass<7>(a, src, dst, first, last, Ns, col0); break;
-      case 8: mixed_pass<8>(a, src, dst, first, last, Ns, col0); break;
-      default: mixed_pass<16>(a, src, dst, first, last, Ns, col0); break;
+      case 2: mixed_pass<2>(a, s, src, dst, first, last, col0); break;
+      case 3: mixed_pass<3>(a, s, src, dst, first, last, col0); break;
+      case 4: mixed_pass<4>(a, s, src, dst, first, last, col0); break;
+      case 5: mixed_pass<5>(a, s, src, dst, first, last, col0); break;
+      case 7: mixed_pass<7>(a, s, src, dst, first, last, col0); break;
+      case 8: mixed_pass<8>(a, s, src, dst, first, last, col0); break;
+      default: mixed_pass<16>(a, s, src, dst, first, last, col0); break;
     }
-    Ns *= a.rad[s];
     __syncthreads();
   }
 }
 
-// Radix schedule: radix-16 passes for 2^a, then one 8/4/2 pass for the rest
-// of 2^a, then the 3s, 5s and 7s.  Returns the number of passes, 0 if N has
-// another prime factor or needs more than kMixedMaxPasses passes.
+// Radix schedule: radix-16 passes for 2^a and one 8/4/2 pass for the rest of
+// 2^a first, then the 3s, 5s and 7s.  The first pass (Ns = 1) needs no
+// twiddles, so it gets the largest radix.  (A bank model prefers the
+// power-of-two radices last -- their first-pass writes at stride 8 or 16
+// conflict -- but measured on GB300 that order is 10-25 % slower: the
+// twiddle loads and products of a radix-16 pass cost more than the
+// conflicts.)  Returns the number of passes, 0 if N has another prime factor
+// or needs more than kMixedMaxPasses passes.
 int mixed_radices(long long N, int* rad) {
   int n = 0;
   long long m = N;
@@ -185,6 +192,17 @@ int mixed_plan_init(fft_plan* p) {
   a.C = N <= 4096 ? (int)(4096 / N) : 1;
   if (a.C > p->batch) a.C = (int)p->batch;
   a.batch = p->batch;
+  {
+    unsigned ns = 1;
+    for (int s = 0; s < a.nrad; ++s) {
+      const unsigned nb = (unsigned)(N / a.rad[s]);
+      a.nb[s] = nb;
+      a.nb_m[s] = nb == 1 ? 0u : (unsigned)((0x100000000ULL + nb - 1) / nb);
+      a.ns[s] = ns;
+      a.ns_m[s] = ns == 1 ? 0u : (unsigned)((0x100000000ULL + ns - 1) / ns);
+      ns *= (unsigned)a.rad[s];
+    }
+  }
   p->mixed_threads = a.C * N <= 4096 ? 256 : 512;
   p->mixed_smem = (int)(2 * (size_t)a.C * (size_t)N * 8);
   if (p->mixed_smem > 48 * 1024 &&
