@@ -23,7 +23,7 @@ Also printed on the same JSON line:
 
 ``--impl reference`` times the oracle instead (the deliberately slow CPU
 baseline) and prints the same line with "impl": "reference".
-Other workloads for measurement only: --workload large | tc | many | range | real | mixed.
+Other workloads for measurement only: --workload large | tc | many | range | real | mixed | fp64.
 """
 from __future__ import annotations
 
@@ -872,6 +872,33 @@ def run_measure(args):
             lib.fft_destroy(h)
         desc = ("mixed-radix lengths (2^a 3^b 5^c 7^d, one on-chip pass): ~2^26 CN(0,1) points per launch; "
                 "cufft_torch = torch.fft (context)")
+    elif args.workload == "fp64":
+        # complex128 transforms in FP64: 2^25 points per launch (512 MiB each way)
+        for n in (1024, 4096, 1000, 5000):
+            batch = (1 << 25) // n
+            g = np.random.Generator(np.random.PCG64(workloads.seed_for(9) + n))
+            xh = g.normal(0, np.sqrt(0.5), (batch, n)) + 1j * g.normal(0, np.sqrt(0.5), (batch, n))
+            x = torch.from_numpy(xh.reshape(-1)).to(dev)
+            y = torch.empty_like(x)
+            h = ctypes.c_void_p(lib.fft_plan_create(n, batch, 0, _lib.FFT_PREC_FP64))
+            us = _time_fn(torch, lambda: run_plan(h, x, y), args.steps, args.warmup, stream) * 1e3
+
+            def cufft():
+                with torch.cuda.stream(stream):
+                    torch.fft.fft(x.view(batch, n))
+
+            cu = _time_fn(torch, cufft, args.steps, args.warmup, stream) * 1e3
+            run_plan(h, x, y)
+            torch.cuda.synchronize()
+            rows = [0, batch - 1]
+            err = float(oracle.rel_l2_rows(y.view(batch, n)[rows].cpu().numpy(), oracle.transform(xh[rows])).max())
+            res.append({"n": n, "batch": batch, "us": round(us, 1), "cufft_torch_us": round(cu, 1),
+                        "gflops_fp64": round(5.0 * n * np.log2(n) * batch / (us * 1e-6) / 1e9, 1),
+                        "hbm_frac": round(32.0 * n * batch / (us * 1e-6) / 1e9 / peak, 4),
+                        "err_sampled": float(f"{err:.3e}")})
+            lib.fft_destroy(h)
+        desc = ("FP64 (complex128) transforms, one on-chip pass: 2^25 CN(0,1) points per launch; HBM fraction "
+                "counts 32 B per point; cufft_torch = torch.fft on complex128 (context)")
     print(json.dumps({"workload": args.workload, "desc": desc, "results": res,
                       "peak_hbm_gbs": peak}), flush=True)
 
@@ -882,7 +909,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range", "real", "mixed"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range", "real", "mixed", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -55,7 +55,11 @@ enum {
   FFT_PREC_TC_BF16 = 1,
   FFT_PREC_TC_FP16 = 2,
   FFT_PREC_TC_BF16_SPLIT = 3,
-  FFT_PREC_TC_FP16_SPLIT = 4
+  FFT_PREC_TC_FP16_SPLIT = 4,
+  /* complex128 data and FP64 arithmetic; 1-D plans of length 2 <= n <= 7168
+   * with n = 2^a 3^b 5^c 7^d (powers of two up to 4096 included), one on-chip
+   * pass; in and out 16-byte aligned */
+  FFT_PREC_FP64 = 5
 };
 
 enum {

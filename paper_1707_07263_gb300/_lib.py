@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbfft.so")
 
 FFT_FORWARD, FFT_INVERSE, FFT_ADJOINT = 0, 1, 2
-FFT_PREC_FP32, FFT_PREC_TC_BF16, FFT_PREC_TC_FP16, FFT_PREC_TC_BF16_SPLIT, FFT_PREC_TC_FP16_SPLIT = range(5)
+FFT_PREC_FP32, FFT_PREC_TC_BF16, FFT_PREC_TC_FP16, FFT_PREC_TC_BF16_SPLIT, FFT_PREC_TC_FP16_SPLIT, FFT_PREC_FP64 = range(6)
 
 FFT_OK = 0
 ERRORS = {

@@ -26,6 +26,7 @@ PREC = {
     "tc_fp16": L.FFT_PREC_TC_FP16,
     "tc_bf16_split": L.FFT_PREC_TC_BF16_SPLIT,
     "tc_fp16_split": L.FFT_PREC_TC_FP16_SPLIT,
+    "fp64": L.FFT_PREC_FP64,
 }
 
 
@@ -98,8 +99,9 @@ class Plan:
 
     def __call__(self, x: torch.Tensor, out: torch.Tensor | None = None, dir: int | None = None,
                  stream=None) -> torch.Tensor:
-        if x.dtype != torch.complex64 or not x.is_cuda:
-            raise TypeError("expected a complex64 CUDA tensor")
+        want = torch.complex128 if self.prec == L.FFT_PREC_FP64 else torch.complex64
+        if x.dtype != want or not x.is_cuda:
+            raise TypeError(f"expected a {want} CUDA tensor")
         x = x.contiguous()
         if out is None:
             out = torch.empty_like(x)
@@ -157,9 +159,10 @@ def clear_plan_cache() -> None:
         _cache.clear()
 
 
-def _check_input(x: torch.Tensor, min_dims: int = 1) -> None:
-    if not isinstance(x, torch.Tensor) or x.dtype != torch.complex64 or not x.is_cuda:
-        raise TypeError("expected a complex64 CUDA tensor")
+def _check_input(x: torch.Tensor, min_dims: int = 1, allow_fp64: bool = False) -> None:
+    ok = (torch.complex64, torch.complex128) if allow_fp64 else (torch.complex64,)
+    if not isinstance(x, torch.Tensor) or x.dtype not in ok or not x.is_cuda:
+        raise TypeError("expected a complex64 CUDA tensor" + (" (or complex128)" if allow_fp64 else ""))
     if x.dim() < min_dims:
         raise ValueError(f"expected at least {min_dims} dimension(s)")
 
@@ -206,16 +209,26 @@ class _FFTMany(torch.autograd.Function):
         return ctx.plan(g.contiguous(), dir=ctx.dir ^ ADJOINT), None, None, None
 
 
-def fft(x: torch.Tensor, prec="fp32") -> torch.Tensor:
-    """Eq. 1 over the last dimension (length a power of two, 2..2^28)."""
-    _check_input(x)
-    return _FFT1d.apply(x, FORWARD, prec)
+def _prec_for(x: torch.Tensor, prec):
+    if x.dtype == torch.complex128:
+        if prec not in (None, "fp64", L.FFT_PREC_FP64):
+            raise ValueError("complex128 tensors run in FP64")
+        return "fp64"
+    return "fp32" if prec is None else prec
 
 
-def ifft(x: torch.Tensor, prec="fp32") -> torch.Tensor:
-    """Eq. 2 over the last dimension."""
-    _check_input(x)
-    return _FFT1d.apply(x, INVERSE, prec)
+def fft(x: torch.Tensor, prec=None) -> torch.Tensor:
+    """Eq. 1 over the last dimension: lengths that are powers of two (2..2^28)
+    or products 2^a 3^b 5^c 7^d up to 14336.  complex64 runs in FP32 (or a
+    tensor-core precision), complex128 in FP64 (lengths up to 7168)."""
+    _check_input(x, allow_fp64=True)
+    return _FFT1d.apply(x, FORWARD, _prec_for(x, prec))
+
+
+def ifft(x: torch.Tensor, prec=None) -> torch.Tensor:
+    """Eq. 2 over the last dimension (same lengths and precisions as fft)."""
+    _check_input(x, allow_fp64=True)
+    return _FFT1d.apply(x, INVERSE, _prec_for(x, prec))
 
 
 def fft2(x: torch.Tensor, prec="fp32") -> torch.Tensor:

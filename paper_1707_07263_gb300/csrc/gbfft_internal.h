@@ -33,10 +33,11 @@ enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3, 
 // Lengths N = 2^a 3^b 5^c 7^d that are not powers of two (mixed.cu).
 constexpr int kMixedMaxPasses = 16;
 constexpr long long kMixedMaxN = 14336;   // two shared-memory buffers of N complex values fit
+constexpr long long kMixedMaxN64 = 7168;  // the same for FP64 (complex128) values
 struct MixedArgs {
-  const float2* in;
-  float2* out;
-  const float2* tw;   // W_N^m, m < N
+  const void* in;     // float2 (FP32) or double2 (FP64) elements
+  void* out;
+  const void* tw;     // W_N^m, m < N, same element type
   int N, C;           // length; transforms per CTA
   long long batch;
   int nrad;
@@ -46,13 +47,14 @@ struct MixedArgs {
   unsigned nb[kMixedMaxPasses], nb_m[kMixedMaxPasses];
   unsigned ns[kMixedMaxPasses], ns_m[kMixedMaxPasses];
   int conj_in, scale_out;
-  float sx, sy;
+  double sx, sy;      // output scale (1/N of Eq. 2 exact to FP64 for the FP64 kernel)
 };
 int mixed_radices(long long N, int* rad);
 int mixed_plan_init(fft_plan* p);
-int mixed_exec(fft_plan* p, const float2* in, float2* out, int conj, float sx, float sy, int scale_out,
+int mixed_exec(fft_plan* p, const void* in, void* out, int conj, double sx, double sy, int scale_out,
                cudaStream_t s);
 cudaError_t launch_gen_twiddles_n(float2* tab, long long N, long long count, cudaStream_t s);
+cudaError_t launch_gen_twiddles_n64(double2* tab, long long N, long long count, cudaStream_t s);
 
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false);
 cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);

@@ -175,7 +175,8 @@ static void free_plan(fft_plan* p) {
 }
 
 static bool valid_dir(int dir) { return dir >= 0 && dir <= 3; }
-static bool valid_prec(int prec) { return prec >= FFT_PREC_FP32 && prec <= FFT_PREC_TC_FP16_SPLIT; }
+static bool valid_prec(int prec) { return prec >= FFT_PREC_FP32 && prec <= FFT_PREC_FP64; }
+static bool tc_prec(int prec) { return prec >= FFT_PREC_TC_BF16 && prec <= FFT_PREC_TC_FP16_SPLIT; }
 
 // Direction -> load/store transform: conjugate direction via conj in/out,
 // 1/N of Eq. 2 folded into the store.
@@ -450,7 +451,8 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
   const float2* fin = (const float2*)in;
   float2* fout = (float2*)out;
   int rc;
-  if (p->prec != FFT_PREC_FP32 && p->kind != KIND_MANY) {
+  if (p->prec == FFT_PREC_FP64 && (((uintptr_t)in & 15) || ((uintptr_t)out & 15))) return FFT_ERR_ALIGN;
+  if (tc_prec(p->prec) && p->kind != KIND_MANY) {
     rc = tc_exec(p, fin, fout, dir, s);
   } else {
     switch (p->kind) {
@@ -469,8 +471,8 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
       case KIND_REAL: rc = exec_real(p, fin, fout, dir, s); break;
       case KIND_MIXED: {
         const DirXf x = dir_xf(dir, p->n);
-        rc = mixed_exec(p, fin, fout, x.conj, x.scale, x.conj ? -x.scale : x.scale,
-                        (x.conj || x.scale != 1.0f) ? 1 : 0, s);
+        const double sc = (dir & FFT_INVERSE) ? 1.0 / (double)p->n : 1.0;
+        rc = mixed_exec(p, in, out, x.conj, sc, x.conj ? -sc : sc, (x.conj || sc != 1.0) ? 1 : 0, s);
         break;
       }
       default: rc = FFT_ERR_INVALID_ARG;
@@ -911,15 +913,24 @@ static int build_2d(fft_plan* p, int ly, int lx) {
 // ============================================================================
 extern "C" {
 
-// Lengths that are not powers of two: 7-smooth N <= kMixedMaxN, one pass.
+// Lengths that are not powers of two (7-smooth N <= kMixedMaxN, FP32), and
+// every FP64 plan (7-smooth N <= kMixedMaxN64, powers of two included): one
+// pass of the mixed-radix kernel.
 static fft_plan* create_mixed(int64_t n, int64_t batch, int dir, int prec) {
   int rad[kMixedMaxPasses];
-  if (n < 3 || n > kMixedMaxN || batch < 1 || !valid_dir(dir) || !valid_prec(prec) || mixed_radices(n, rad) == 0 ||
-      (double)n * (double)batch > 9.0e15) {
+  const bool fp64 = prec == FFT_PREC_FP64;
+  const bool pow2 = n > 0 && (n & (n - 1)) == 0;
+  if (n < 2 || batch < 1 || !valid_dir(dir) || !valid_prec(prec) || (double)n * (double)batch > 9.0e15) {
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
   }
-  if (prec != FFT_PREC_FP32) {
+  const bool smooth = pow2 || (n <= kMixedMaxN && mixed_radices(n, rad) != 0);
+  if (!smooth || (!fp64 && n > kMixedMaxN) || (pow2 && n > (1LL << FFT_MAX_LOG2N))) {
+    set_err(FFT_ERR_INVALID_ARG);
+    return nullptr;
+  }
+  if (tc_prec(prec) || (fp64 && n > kMixedMaxN64)) {
+    // valid lengths this build does not run at that precision
     set_err(FFT_ERR_UNSUPPORTED);
     return nullptr;
   }
@@ -944,6 +955,13 @@ static fft_plan* create_mixed(int64_t n, int64_t batch, int dir, int prec) {
 
 static fft_plan* create_1d(int64_t n, int64_t batch, int dir, int prec, const fft_plan_config* cfg) {
   const int lgN = ilog2_exact(n);
+  if (prec == FFT_PREC_FP64) {
+    if (cfg) {
+      set_err(FFT_ERR_UNSUPPORTED);
+      return nullptr;
+    }
+    return create_mixed(n, batch, dir, prec);
+  }
   if (lgN < 0 && n > 2 && !cfg) return create_mixed(n, batch, dir, prec);
   if (lgN < 1 || lgN > FFT_MAX_LOG2N || batch < 1 || !valid_dir(dir) || !valid_prec(prec)) {
     set_err(FFT_ERR_INVALID_ARG);
@@ -1085,6 +1103,10 @@ fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
   }
+  if (prec == FFT_PREC_FP64) {
+    set_err(FFT_ERR_UNSUPPORTED);
+    return nullptr;
+  }
   if (prec != FFT_PREC_FP32) {
     set_err(FFT_ERR_UNSUPPORTED);
     return nullptr;
@@ -1117,6 +1139,11 @@ fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, i
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
   }
+  if (prec == FFT_PREC_FP64) {
+    set_err(FFT_ERR_UNSUPPORTED);
+    return nullptr;
+  }
+
   if (prec != FFT_PREC_FP32) {
     set_err(FFT_ERR_UNSUPPORTED);
     return nullptr;

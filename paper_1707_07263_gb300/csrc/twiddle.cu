@@ -56,6 +56,23 @@ cudaError_t launch_gen_twiddles_n(float2* tab, long long N, long long count, cud
   return cudaGetLastError();
 }
 
+// tab[m] = W_N^m in FP64, m < count (FP64 transforms).
+__global__ void gen_twiddles_n64(double2* tab, long long N, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)(i % N) / (double)N, &sn, &cs);
+    tab[i] = make_double2(cs, sn);
+  }
+}
+
+cudaError_t launch_gen_twiddles_n64(double2* tab, long long N, long long count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const long long blocks = (count + 255) / 256;
+  gen_twiddles_n64<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(tab, N, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev) {
   const int total = stage_tw_size(lg, rev);
   if (total == 0) return cudaSuccess;
