@@ -56,14 +56,21 @@ def measured_peaks():
     return HBM_FALLBACK, "fallback"
 
 
+# The sources the benchmark's kernels are compiled from (the single-pass
+# register, prefetching and TMA-staged kernels and what they include).  The
+# DRAM traffic recorded in profiles/traffic.json is valid only while these
+# files are unchanged.
+BENCH_KERNEL_SOURCES = ("fft_common.cuh", "tile_fft.cuh", "tile_fft_tma.cuh", "tile_registry.h", "tile_inst_jj.cu",
+                        "tile_inst_pf.cu", "tile_inst_tma.cu")
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1707_07263_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    for name in BENCH_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
