@@ -101,7 +101,7 @@ struct fft_plan {
 
   // mixed-radix plans (KIND_MIXED)
   gbfft::MixedArgs mixed;
-  int mixed_threads, mixed_smem;
+  int mixed_threads, mixed_smem, mixed_pad;
   const float2* pre_tw;               // its W_N^n table, n < N/2
   long long tma_grid;                 // its resident-CTA grid
 

@@ -182,12 +182,49 @@ __device__ __forceinline__ void dft_any(T* v) {
     gdft_pow2<R>(v);
 }
 
+// Twiddles w^r, r = 1..R-1, of one butterfly (w = W_N^e, e = k * stride).
+// FP32: the powers w, w^2, w^4, w^8 that the radix needs are loaded from the
+// W_N^m table, the others are products of them (radix 16: 4 loads + 11
+// products instead of 15 loads; radix 5: 2 + 2; radix 7: 3 + 3); measured
+// 2-16 % faster.  FP64: every power is loaded (FP64 products are the scarce
+// resource; the product form measured 5-10 % slower).
+template <int R, typename T>
+__device__ __forceinline__ void mixed_twiddles(T* v, const T* tw, int e) {
+  if constexpr (std::is_same_v<T, double2>) {
+    // FP64 products cost far more than loads on this GPU: load every power
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = gmul(v[r], __ldg(tw + r * e));
+    return;
+  }
+  T w[R];
+  w[1] = __ldg(tw + e);
+  if constexpr (R >= 3) w[2] = __ldg(tw + 2 * e);
+  if constexpr (R >= 5) w[4] = __ldg(tw + 4 * e);
+  if constexpr (R >= 9) w[8] = __ldg(tw + 8 * e);
+  if constexpr (R >= 4) w[3] = gmul(w[1], w[2]);
+  if constexpr (R >= 6) w[5] = gmul(w[4], w[1]);
+  if constexpr (R >= 7) w[6] = gmul(w[4], w[2]);
+  if constexpr (R >= 8) w[7] = gmul(w[4], w[3]);
+  if constexpr (R >= 16) {
+#pragma unroll
+    for (int r = 1; r < 8; ++r) w[8 + r] = gmul(w[8], w[r]);
+  }
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = gmul(v[r], w[r]);
+}
+
+// Shared-memory index of tile element n: padded by one entry every 16 when
+// PAD (conflict-free strided writes of a leading radix-8/16 pass, chosen per
+// plan from a bank model of every pass), identity otherwise.
+template <bool PAD>
+__device__ __forceinline__ int msidx(int n) { return PAD ? n + (n >> 4) : n; }
+
 // n / d from the reciprocal m = ceil(2^32 / d) (m = 0 stands for d = 1)
 __device__ __forceinline__ unsigned fdiv(unsigned n, unsigned m) { return m ? __umulhi(n, m) : n; }
 
 // One pass s over the tile: C transforms of length N at src (global when
 // FIRST, else shared memory), written to dst (global when LAST).
-template <int R, typename T>
+template <int R, bool PAD, typename T>
 __device__ __forceinline__ void mixed_pass(const MixedArgs& a, int s, const T* src, T* dst, bool first, bool last,
                                            long long col0) {
   using S = typename Cx<T>::S;
@@ -200,13 +237,13 @@ __device__ __forceinline__ void mixed_pass(const MixedArgs& a, int s, const T* s
     const int c = (int)fdiv((unsigned)b, nbm), j = b - c * (int)NB;
     const bool ok = col0 + c < a.batch;
     T v[R];
-    const T* sp = src + (long long)c * N + j;
+    const int n0 = c * N + j;   // tile index of input r = 0
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (first)
-        v[r] = ok ? __ldcs(sp + r * NB) : Cx<T>::make(0, 0);
+        v[r] = ok ? __ldcs(src + n0 + r * NB) : Cx<T>::make(0, 0);
       else
-        v[r] = sp[r * NB];
+        v[r] = src[msidx<PAD>(n0 + r * (int)NB)];
     }
     if (first && a.conj_in) {
 #pragma unroll
@@ -214,61 +251,64 @@ __device__ __forceinline__ void mixed_pass(const MixedArgs& a, int s, const T* s
     }
     const int jq = (int)fdiv((unsigned)j, nsm);
     const int k = j - jq * (int)Ns;
-    if (Ns > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = gmul(v[r], __ldg(tw + r * k * stride));
-    }
+    if (Ns > 1) mixed_twiddles<R>(v, tw, k * stride);
     dft_any<R>(v);
-    const int base = jq * (int)Ns * R + k;
-    T* d = dst + (long long)c * N + base;
+    const int m0 = c * N + jq * (int)Ns * R + k;   // tile index of output q = 0
     if (last) {
       if (!ok) continue;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         T y = v[q];
         if (a.scale_out) y = Cx<T>::make(y.x * (S)a.sx, y.y * (S)a.sy);
-        __stcs(d + q * Ns, y);
+        __stcs(dst + m0 + q * (int)Ns, y);
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < R; ++q) d[q * Ns] = v[q];
+      for (int q = 0; q < R; ++q) dst[msidx<PAD>(m0 + q * (int)Ns)] = v[q];
     }
   }
 }
 
-template <typename T>
+template <typename T, bool PAD>
 __device__ __forceinline__ void mixed_tile(const MixedArgs& a, T* smem) {
   const long long tile = blockIdx.x;
   const long long col0 = tile * a.C;
   const long long off = col0 * a.N;
   const T* in = (const T*)a.in + off;
   T* out = (T*)a.out + off;
-  T* const buf1 = smem + (size_t)a.C * a.N;
+  T* const buf1 = smem + msidx<PAD>(a.C * a.N - 1) + 1;
   for (int s = 0; s < a.nrad; ++s) {
     const bool first = s == 0, last = s == a.nrad - 1;
     const T* src = first ? in : ((s & 1) ? smem : buf1);
     T* dst = last ? out : ((s & 1) ? buf1 : smem);
     switch (a.rad[s]) {
-      case 2: mixed_pass<2>(a, s, src, dst, first, last, col0); break;
-      case 3: mixed_pass<3>(a, s, src, dst, first, last, col0); break;
-      case 4: mixed_pass<4>(a, s, src, dst, first, last, col0); break;
-      case 5: mixed_pass<5>(a, s, src, dst, first, last, col0); break;
-      case 7: mixed_pass<7>(a, s, src, dst, first, last, col0); break;
-      case 8: mixed_pass<8>(a, s, src, dst, first, last, col0); break;
-      default: mixed_pass<16>(a, s, src, dst, first, last, col0); break;
+      case 2: mixed_pass<2, PAD>(a, s, src, dst, first, last, col0); break;
+      case 3: mixed_pass<3, PAD>(a, s, src, dst, first, last, col0); break;
+      case 4: mixed_pass<4, PAD>(a, s, src, dst, first, last, col0); break;
+      case 5: mixed_pass<5, PAD>(a, s, src, dst, first, last, col0); break;
+      case 7: mixed_pass<7, PAD>(a, s, src, dst, first, last, col0); break;
+      case 8: mixed_pass<8, PAD>(a, s, src, dst, first, last, col0); break;
+      default: mixed_pass<16, PAD>(a, s, src, dst, first, last, col0); break;
     }
     __syncthreads();
   }
 }
 
 // FP32: two resident CTAs of up to 512 threads (64 registers); FP64: one.
+template <bool PAD>
 __global__ void __launch_bounds__(512, 2) mixed_kernel(const MixedArgs a) {
   extern __shared__ __align__(16) unsigned char mixed_smem[];
-  mixed_tile<float2>(a, (float2*)mixed_smem);
+  mixed_tile<float2, PAD>(a, (float2*)mixed_smem);
 }
+template <bool PAD>
 __global__ void __launch_bounds__(512, 1) mixed_kernel64(const MixedArgs a) {
   extern __shared__ __align__(16) unsigned char mixed_smem[];
-  mixed_tile<double2>(a, (double2*)mixed_smem);
+  mixed_tile<double2, PAD>(a, (double2*)mixed_smem);
+}
+
+static const void* mixed_fn(bool fp64, bool pad) {
+  return fp64 ? (pad ? (const void*)mixed_kernel64<true> : (const void*)mixed_kernel64<false>)
+              : (pad ? (const void*)mixed_kernel<true> : (const void*)mixed_kernel<false>);
 }
 
 // Radix schedule: radix-16 passes for 2^a and one 8/4/2 pass for the rest of
@@ -325,8 +365,16 @@ int mixed_plan_init(fft_plan* p) {
     }
   }
   p->mixed_threads = a.C * N <= tile ? 256 : 512;
-  p->mixed_smem = (int)(2 * (size_t)a.C * (size_t)N * esz);
-  const void* fn = fp64 ? (const void*)mixed_kernel64 : (const void*)mixed_kernel;
+  // padding pays when a radix-8 or -16 pass leads (its writes are strided by
+  // the radix); pure odd-radix lengths keep the unpadded layout
+  // (when the padded buffers fit in shared memory)
+  const size_t pts = (size_t)a.C * (size_t)N;
+  const size_t padded = pts + ((pts - 1) >> 4) + 1;
+  p->mixed_pad = (a.rad[0] >= 8 && 2 * padded * esz <= 227 * 1024) ? 1 : 0;
+  const size_t buf = p->mixed_pad ? padded : pts;
+  p->mixed_smem = (int)(2 * buf * esz);
+  if (p->mixed_smem > 227 * 1024) return FFT_ERR_UNSUPPORTED;
+  const void* fn = mixed_fn(fp64, p->mixed_pad);
   if (p->mixed_smem > 48 * 1024 &&
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->mixed_smem) != cudaSuccess)
     return FFT_ERR_UNSUPPORTED;
@@ -358,7 +406,7 @@ int mixed_exec(fft_plan* p, const void* in, void* out, int conj, double sx, doub
   const long long tiles = (p->batch + a.C - 1) / a.C;
   if (tiles > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
   void* args[] = {(void*)&a};
-  const void* fn = p->prec == FFT_PREC_FP64 ? (const void*)mixed_kernel64 : (const void*)mixed_kernel;
+  const void* fn = mixed_fn(p->prec == FFT_PREC_FP64, p->mixed_pad);
   return cudaLaunchKernel(fn, dim3((unsigned)tiles), dim3(p->mixed_threads), args, (size_t)p->mixed_smem, s) ==
                  cudaSuccess
              ? FFT_OK
