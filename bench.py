@@ -158,6 +158,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of every rank's value (the job takes as long as its
+    slowest rank); the value itself without a process group."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -365,10 +376,7 @@ def run_gpu(args):
     ms_total = t0e.elapsed_time(t1e)
     per_item_ms = [float(np.mean([evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(K)]))
                    for i in range(len(items))]
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / K
     step_flop = sum(flops(n, b) for _, n, b, _ in items)
     value = step_flop * world / (ms_step * 1e-3) / 1e9
@@ -433,11 +441,7 @@ def run_gpu(args):
                 e2e_step()
             a1.record(stream)
             torch.cuda.synchronize()
-            ms = a0.elapsed_time(a1) / ke
-            if dist:
-                t = torch.tensor([ms], device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                ms = float(t.item())
+            ms = max_over_ranks(a0.elapsed_time(a1) / ke, dist, dev)
             return ms, sorted({pp.last_mode for pp in pipes})
 
         # streaming calls on shared streams: the copy pipeline overlaps the
