@@ -581,9 +581,13 @@ def run_case(args):
     import torch
     from paper_1707_07263_gb300 import _lib
     lib = _lib.load()
-    n = 1 << args.case
-    batch = args.batch or max(1, TOTAL // n)
-    h = lib.fft_plan_create(n, batch, args.dir, args.prec)
+    n = args.case_n or (1 << args.case)
+    fp64 = args.prec == _lib.FFT_PREC_FP64
+    batch = args.batch or max(1, (TOTAL // 2 if fp64 else TOTAL) // n)
+    if args.real:
+        h = lib.fft_plan_create_r2c(n, batch, args.prec)
+    else:
+        h = lib.fft_plan_create(n, batch, args.dir, args.prec)
     if not h:
         raise RuntimeError(_lib.ERRORS.get(lib.fft_last_error()))
     h = ctypes.c_void_p(h)
@@ -591,10 +595,19 @@ def run_case(args):
     wsb = torch.empty(ws, dtype=torch.uint8, device="cuda") if ws else None
     if ws:
         _lib.check(lib.fft_plan_set_workspace(h, ctypes.c_void_p(wsb.data_ptr())))
-    x = torch.randn(n * batch, dtype=torch.complex64, device="cuda")
-    y = torch.empty_like(x)
+    if args.real:
+        # real rows of n floats and rows of n/2 + 1 complex values; --dir picks the direction
+        xr = torch.randn(n * batch, dtype=torch.float32, device="cuda")
+        xc = torch.randn((n // 2 + 1) * batch, dtype=torch.complex64, device="cuda")
+        x, y = (xr, xc) if args.dir == 0 else (xc, xr)
+    else:
+        x = torch.randn(n * batch, dtype=torch.complex128 if fp64 else torch.complex64, device="cuda")
+        y = torch.empty_like(x)
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    if args.filter:
+    if args.real:
+        def one():
+            _lib.check(lib.fft_exec_dir(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), args.dir, s))
+    elif args.filter:
         # range compression with a random filter (fft_exec_filter)
         H = torch.randn(n, dtype=torch.complex64, device="cuda")
 
@@ -616,8 +629,10 @@ def run_case(args):
     ms = e0.elapsed_time(e1) / args.steps
     buf = ctypes.create_string_buffer(512)
     lib.fft_plan_describe(h, buf, 512)
-    print(json.dumps({"case": f"2^{args.case} x {batch}", "us": round(ms * 1e3, 2),
-                      "hbm_gbs_per_launch": round(16.0 * n * batch * lib.fft_plan_launches(h) / (ms * 1e-3) / 1e9, 1),
+    # algorithmic bytes per transform: one read and one write of every value
+    bytes_pt = (4.0 * n + 8.0 * (n // 2 + 1)) if args.real else (32.0 if fp64 else 16.0) * n
+    print(json.dumps({"case": f"{n} x {batch}", "us": round(ms * 1e3, 2),
+                      "hbm_gbs_per_launch": round(bytes_pt * batch * lib.fft_plan_launches(h) / (ms * 1e-3) / 1e9, 1),
                       "plan": buf.value.decode()}))
     lib.fft_destroy(h)
 
@@ -930,10 +945,12 @@ def main():
     ap.add_argument("--dir", type=int, default=0)
     ap.add_argument("--prec", type=int, default=0)
     ap.add_argument("--filter", action="store_true", help="with --case: range compression instead of the FFT")
+    ap.add_argument("--case-n", type=int, default=0, help="profiling case of any supported length n")
+    ap.add_argument("--real", action="store_true", help="with --case/--case-n: a real-data plan (--dir 0 r2c, 1 c2r)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.case:
+    if args.case or args.case_n:
         run_case(args)
     elif args.workload != "cfg2" and args.impl != "reference":
         run_measure(args)

@@ -233,6 +233,7 @@ __device__ __forceinline__ void mixed_pass(const MixedArgs& a, int s, const T* s
   const unsigned NB = a.nb[s], nbm = a.nb_m[s], Ns = a.ns[s], nsm = a.ns_m[s];
   const int total = a.C * (int)NB;
   const int stride = N / ((int)Ns * R);
+  const S sx = (S)a.sx, sy = (S)a.sy;   // converted once: no FP64 work in the FP32 kernel
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
     const int c = (int)fdiv((unsigned)b, nbm), j = b - c * (int)NB;
     const bool ok = col0 + c < a.batch;
@@ -259,7 +260,7 @@ __device__ __forceinline__ void mixed_pass(const MixedArgs& a, int s, const T* s
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         T y = v[q];
-        if (a.scale_out) y = Cx<T>::make(y.x * (S)a.sx, y.y * (S)a.sy);
+        if (a.scale_out) y = Cx<T>::make(y.x * sx, y.y * sy);
         __stcs(dst + m0 + q * (int)Ns, y);
       }
     } else {
