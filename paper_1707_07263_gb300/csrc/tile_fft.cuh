@@ -420,13 +420,14 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
     if (Cfg::EPI && a.ft_lgN) {
       // four-step twiddle W_N^{n2*k}, n2 = col0 + c, k = j + q*NS
       //   = W_N^{n2*j} * W_N^{n2*NS*q}; the second factor is the per-column
-      //   table epi_tab[c*16 + q] built at kernel start.
+      //   table epi_tab[q*C + c] built at kernel start (q-major: adjacent
+      //   lanes of the c-fast mapping read adjacent entries, no bank conflict).
       const unsigned n2 = a.ft_by_batch ? (unsigned)bidx : (unsigned)(col0 + c);
       const unsigned m = n2 * (unsigned)j;
       const unsigned mask = (1u << a.ft_s) - 1u;
       const float2 base = cmul(__ldg(a.ft_lo + (m & mask)), __ldg(a.ft_hi + (m >> a.ft_s)));
 #pragma unroll
-      for (int q = 0; q < R; ++q) v[q] = cmul(v[q], cmul(base, epi_tab[c * 16 + q]));
+      for (int q = 0; q < R; ++q) v[q] = cmul(v[q], cmul(base, epi_tab[q * C + c]));
     }
     if constexpr (!IN_CF && OUT_CF && !OFFS && PRE == 0) {
       if (a.filt) {
@@ -511,7 +512,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, flo
     // per-column step factors W_N^{n2*NS_last*q}, q = 0..15
     constexpr int NS_LAST = 1 << radix_lgns(LG, Cfg::NST - 1);
     for (int e = threadIdx.x; e < C * 16; e += Cfg::T) {
-      const int c = e >> 4, q = e & 15;
+      const int q = e / C, c = e - q * C;   // entry q*C + c
       const unsigned n2 = a.ft_by_batch ? (unsigned)b : (unsigned)(col0 + c);
       const unsigned m = n2 * (unsigned)NS_LAST * (unsigned)q;
       const unsigned mm = m & ((1u << a.ft_lgN) - 1u);

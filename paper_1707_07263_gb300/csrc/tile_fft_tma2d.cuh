@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(ColTmaCfg<LG, C>::T, ColTmaCfg<LG, C>::MIN_BLO
     if (a.ft_lgN) {
       constexpr int NS_LAST = 1 << radix_lgns(LG, Tile::NST - 1);
       for (int e = tid; e < C * 16; e += Cfg::T) {
-        const int c = e >> 4, q = e & 15;
+        const int q = e / C, c = e - q * C;   // entry q*C + c (q-major, as tile_pass reads it)
         const unsigned n2 = a.ft_by_batch ? (unsigned)b : (unsigned)(col0 + c);
         const unsigned m = (n2 * (unsigned)NS_LAST * (unsigned)q) & ((1u << a.ft_lgN) - 1u);
         const unsigned mask = (1u << a.ft_s) - 1u;
