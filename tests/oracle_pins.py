@@ -70,6 +70,42 @@ def check_golden(lib):
                 f"golden {c['name']} via {fn.__name__}: {got} vs {c['out']}"
 
 
+GOLDEN_REAL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "real_and_filter_worked_examples.txt")
+
+
+def load_golden_real():
+    cases, cur = [], None
+    with open(GOLDEN_REAL) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tok = line.split()
+            if tok[0] == "example":
+                cur = {"name": tok[1], "kind": tok[2], "n": int(tok[3])}
+                cases.append(cur)
+            elif tok[0] in ("in", "out", "filt"):
+                cur[tok[0]] = np.array([complex(float(p.split(",")[0]), float(p.split(",")[1])) for p in tok[1:]],
+                                       dtype=np.complex128)
+    return cases
+
+
+def check_golden_real_and_filter(lib):
+    cases = load_golden_real()
+    assert {c["kind"] for c in cases} == {"rfft", "irfft", "rc"}
+    for c in cases:
+        n = c["n"]
+        if c["kind"] == "rfft":
+            got = oracle.rfft(c["in"].real, lib=lib)
+        elif c["kind"] == "irfft":
+            got = oracle.irfft(c["in"], n, lib=lib)
+        else:
+            got = oracle.range_compress(c["in"], c["filt"], lib=lib)
+        assert np.max(np.abs(got - c["out"])) <= 1e-12 * max(1.0, np.max(np.abs(c["out"]))), \
+            f"golden {c['name']}: {got} vs {c['out']}"
+
+
 def check_small_by_hand(lib):
     a, b = 0.3 - 1.1j, -2.0 + 0.5j
     for fn in (oracle.dft, oracle.fft):
@@ -287,4 +323,4 @@ def check_mixed_lengths(lib):
 
 ALL_CHECKS = (check_golden, check_small_by_hand, check_closed_forms, check_invariants,
               check_dft_vs_fft, check_numpy, check_fft2, check_range_compress, check_real_transforms,
-              check_mixed_lengths)
+              check_mixed_lengths, check_golden_real_and_filter)
