@@ -198,7 +198,8 @@ GBFFT_API int fft_plan_get_config(const fft_plan* plan, fft_plan_config* out);
  * (>= n*batch*8 bytes), and writes the fastest configuration to *best and its
  * mean time in microseconds to *best_us.  Synchronises `stream`.  The buffers'
  * contents are overwritten.  Plans are created and destroyed internally, so
- * call it outside any stream capture.  Only FFT_PREC_FP32 has choices. */
+ * call it outside any stream capture.  Only FFT_PREC_FP32 power-of-two
+ * lengths have choices (mixed-radix and FP64 plans take no configuration). */
 GBFFT_API int fft_autotune(int64_t n, int64_t batch, int prec, void* in, void* out, void* ws, size_t ws_bytes,
                            void* stream, int iters, fft_plan_config* best, float* best_us);
 

@@ -144,7 +144,9 @@ def get_plan(kind: str, shape, batch: int, prec="fp32", device=None, lengths=Non
         p = _cache.get(key)
         if p is None:
             config = None
-            if tuned and kind == "1d":
+            n0 = int(shape[0])
+            tunable = n0 > 1 and (n0 & (n0 - 1)) == 0 and _prec_code(prec) != L.FFT_PREC_FP64
+            if tuned and kind == "1d" and tunable:   # mixed-radix and FP64 plans take no configuration
                 from . import tune
                 config = tune.tuned_config(int(shape[0]), int(batch), _prec_code(prec), dev)
             p = Plan(kind, shape, batch, FORWARD, prec, dev, lengths, config=config)
