@@ -119,3 +119,65 @@ def test_python_api_fails_loudly_without_cuda_tensor():
         gb.rfft(torch.zeros(16, dtype=torch.float32))
     with pytest.raises(TypeError):
         gb.irfft(torch.zeros(9, dtype=torch.complex64))
+
+
+def test_plan_create_many_rejects_bad_lengths(lib):
+    for bad in ((16, 3), (16, 1), (16, 1 << 17), (0, 16), (16, -32)):
+        arr = (ctypes.c_int64 * len(bad))(*bad)
+        assert lib.fft_plan_create_many(arr, len(bad), 0, 0) is None, bad
+        assert lib.fft_last_error() == -1
+
+
+def test_noalloc_rejects_before_launching(lib):
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    odd = ctypes.c_void_p(p.value + 4)
+    assert lib.fft_exec_noalloc(1000, 1, 0, p, p, None) == -1        # not a power of two
+    assert lib.fft_exec_noalloc(1 << 14, 1, 0, p, p, None) == -1     # below 2^15
+    assert lib.fft_exec_noalloc(1 << 23, 1, 0, p, p, None) == -1     # above 2^22
+    assert lib.fft_exec_noalloc(1 << 16, 1 << 7, 0, p, p, None) == -1  # n * batch above 2^22
+    assert lib.fft_exec_noalloc(1 << 16, 0, 0, p, p, None) == -1
+    assert lib.fft_exec_noalloc(1 << 16, 1, 4, p, p, None) == -1     # unknown direction
+    assert lib.fft_exec_noalloc(1 << 16, 1, 0, None, p, None) == -1
+    assert lib.fft_exec_noalloc(1 << 16, 1, 0, odd, p, None) == -2   # 8-byte alignment
+
+
+def test_null_plan_queries(lib):
+    from paper_1707_07263_gb300 import _lib
+    cfg = _lib.FftPlanConfig()
+    assert lib.fft_plan_get_config(None, ctypes.byref(cfg)) == -1
+    buf = ctypes.create_string_buffer(64)
+    assert lib.fft_plan_describe(None, buf, 64) == -1
+    assert lib.fft_status(None, None) == -1
+    assert lib.fft_plan_length(None) == 0 and lib.fft_plan_batch(None) == 0
+
+
+def test_autotune_rejects_before_running(lib):
+    from paper_1707_07263_gb300 import _lib
+    cfg = _lib.FftPlanConfig()
+    us = ctypes.c_float()
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    for n, batch, iters in ((1000, 1, 5), (1024, 0, 5), (1024, 1, 0)):
+        assert lib.fft_autotune(n, batch, 0, p, p, p, 64, None, iters, ctypes.byref(cfg), ctypes.byref(us)) == -1
+    assert lib.fft_autotune(1024, 1, 0, None, p, p, 64, None, 5, ctypes.byref(cfg), ctypes.byref(us)) == -1
+
+
+def test_fp64_and_mixed_length_limits(lib):
+    from paper_1707_07263_gb300 import _lib
+    fp64 = _lib.FFT_PREC_FP64
+    assert lib.fft_plan_create(8192, 1, 0, fp64) is None        # power of two beyond one FP64 pass
+    assert lib.fft_last_error() == -6
+    assert lib.fft_plan_create(13 * 16, 1, 0, fp64) is None     # prime factor 13
+    assert lib.fft_last_error() == -1
+    assert lib.fft_plan_create(1, 1, 0, fp64) is None
+    assert lib.fft_last_error() == -1
+    assert lib.fft_plan_create(14337, 1, 0, 0) is None          # beyond the mixed-radix limit
+    assert lib.fft_last_error() == -1
+    assert lib.fft_plan_create_2d(64, 64, 1, 0, fp64) is None   # FP64 2-D is not built
+    assert lib.fft_last_error() == -6
+    arr = (ctypes.c_int64 * 2)(16, 32)
+    assert lib.fft_plan_create_many(arr, 2, 0, fp64) is None
+    assert lib.fft_last_error() == -6
+    assert lib.fft_plan_create_r2c(16, 1, fp64) is None
+    assert lib.fft_last_error() == -6
