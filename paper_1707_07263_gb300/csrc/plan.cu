@@ -279,13 +279,16 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
 }
 
 // Attach the tensor-TMA variant to every column pass that has one, when
-// asked for (config tma = 1 on a multi-pass plan, or GBFFT_COLTMA=1).
-// Measured on GB300 it is correct but no faster than the register path for
-// these strided tiles (their DRAM pattern, not load latency, limits them), so
-// it is off by default and left to the autotuner.  Whether a given exec can
-// use it (alignment, strides) is decided per call.
+// asked for (config tma = 1, the default of FP32 1-D multi-pass plans;
+// GBFFT_COLTMA=1 / 0 forces it on / off).  Measured on GB300 once the column
+// tiles' step table stopped conflicting in shared memory, it is the faster
+// column pass at every multi-pass length (autotuner: 2^16 395 -> 328 us,
+// 2^20 499 -> 427, 2^24 639 -> 514, 2^26 690 -> 580 per 2^26 points).
+// Whether a given exec can use it (alignment, strides) is decided per call.
 static int attach_coltma(fft_plan* p, bool want) {
-  if (!want && !env_int("GBFFT_COLTMA", 0)) return FFT_OK;
+  const int env = env_int("GBFFT_COLTMA", -1);
+  if (env >= 0) want = env > 0;
+  if (!want) return FFT_OK;
   for (int i = 0; i < p->npass; ++i) {
     PassDesc& d = p->pass[i];
     if (d.k->map != MAP_CC) continue;
@@ -611,7 +614,8 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     return build_tables(p, lgN, 0, 0);
   }
   p->kind = KIND_FOURSTEP;
-  int npass = cfg->npass >= 2 ? cfg->npass : ((lgN >= 23) ? 3 : 2);
+  // measured on GB300 (autotuner): three passes 2^8 * 2^8 * rest from 2^22 up
+  int npass = cfg->npass >= 2 ? cfg->npass : ((lgN >= 22) ? 3 : 2);
   const int force_np = env_int("GBFFT_PASSES", 0);
   if (cfg->npass < 2 && (force_np == 2 || force_np == 3)) npass = force_np;
   if (npass == 3 && lgN < 3) return FFT_ERR_UNSUPPORTED;
@@ -682,16 +686,16 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     p->npass = 2;
     p->launches = 2;
     p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
-    return attach_coltma(p, cfg->tma > 0);
+    return attach_coltma(p, cfg->tma > 0 || (cfg->tma < 0 && p->prec == FFT_PREC_FP32));
   }
   // three passes, N = N1 * N2 * N3 (M = N2 * N3):
   //   A  columns of length N1 over stride M, scaled by W_N^{m*k1}     in -> ws
   //   B  per k1, columns of length N2 over stride N3 of the M-point
   //      row, scaled by W_M^{n3*k2}                                   ws -> ws (in place)
   //   C  rows of length N3, written to X[k1 + N1*k2 + N1*N2*k3]      ws -> out
-  // measured on GB300: 2^8 x 2^8 x rest up to 2^28 (rest <= 2^12)
-  int l1 = (lgN >= 23 && lgN <= 28) ? 8 : (lgN + 2) / 3;
-  int l2 = (lgN >= 23 && lgN <= 28) ? 8 : (lgN - l1 + 1) / 2;
+  // measured on GB300: 2^8 x 2^8 x rest from 2^22 to 2^28 (rest <= 2^12)
+  int l1 = (lgN >= 22 && lgN <= 28) ? 8 : (lgN + 2) / 3;
+  int l2 = (lgN >= 22 && lgN <= 28) ? 8 : (lgN - l1 + 1) / 2;
   if (cfg->lg1 > 0) {
     l1 = cfg->lg1;
     l2 = cfg->lg2 > 0 ? cfg->lg2 : (lgN - l1 + 1) / 2;
@@ -780,7 +784,7 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   p->npass = 3;
   p->launches = 3;
   p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
-  return attach_coltma(p, cfg->tma > 0);
+  return attach_coltma(p, cfg->tma > 0 || (cfg->tma < 0 && p->prec == FFT_PREC_FP32));
 }
 
 // 2-D plan (Sec. 2.3.2: rows, then columns).  Rows: one on-chip pass over all

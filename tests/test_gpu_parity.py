@@ -157,6 +157,19 @@ def test_fourstep_forward(lib, lg):
     assert_rows(got, oracle_dir(x, 0), tol32(n), f"four-step fwd N=2^{lg}")
 
 
+@pytest.mark.parametrize("lg,passes", [(15, 2), (17, 2), (20, 2), (22, 3), (23, 3)])
+@pytest.mark.parametrize("d", ["fwd", "inv"])
+def test_fourstep_register_columns(lib, monkeypatch, lg, passes, d):
+    """The column passes from registers instead of tensor-TMA boxes (the
+    default multi-pass plans stage them by TMA)."""
+    monkeypatch.setenv("GBFFT_COLTMA", "0")
+    monkeypatch.setenv("GBFFT_PASSES", str(passes))
+    n = 1 << lg
+    x = workloads.cgauss(n, 1, seed=3100 + lg)
+    got = run_1d(lib, x, DIRS[d])
+    assert_rows(got, oracle_dir(x, DIRS[d]), tol32(n), f"register columns N=2^{lg} {d}")
+
+
 @pytest.mark.parametrize("lg", [15, 19])
 @pytest.mark.parametrize("d", ["inv", "adj", "adj_inv"])
 def test_fourstep_directions(lib, lg, d):
@@ -186,7 +199,7 @@ def test_fourstep_other_splits(lib, monkeypatch, split):
 @pytest.mark.parametrize("lg,batch", [(15, 2), (18, 2), (21, 1), (23, 1)])
 @pytest.mark.parametrize("d", ["fwd", "inv"])
 def test_three_pass_split(lib, monkeypatch, lg, batch, d):
-    """N = N1*N2*N3 in three passes (the default from 2^23 up), forced at
+    """N = N1*N2*N3 in three passes (the default from 2^22 up), forced at
     smaller sizes too."""
     monkeypatch.setenv("GBFFT_PASSES", "3")
     n = 1 << lg
@@ -278,7 +291,7 @@ def test_2d_one_column_pass_forced(lib, monkeypatch):
 
 @pytest.mark.parametrize("ny,nx,batch", [(4096, 64, 2), (256, 512, 1), (2048, 16, 3)])
 def test_2d_tensor_tma_columns(lib, monkeypatch, ny, nx, batch):
-    """Column passes staged by tensor-TMA boxes (opt-in path)."""
+    """Column passes staged by tensor-TMA boxes (opt-in for 2-D plans)."""
     monkeypatch.setenv("GBFFT_COLTMA", "1")
     x = workloads.cgauss(ny * nx, batch, seed=ny + nx + 7).reshape(batch, ny, nx)
     got = run_2d(lib, x, 1)
