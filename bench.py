@@ -98,6 +98,19 @@ def ncu_traffic(kernel_key: str):
     return None if e is None else float(e["dram_bytes_per_launch"])
 
 
+def smi_gpu_id(local: int) -> str:
+    """nvidia-smi's name for CUDA device `local`: its UUID (indices differ
+    from CUDA's when CUDA_VISIBLE_DEVICES remaps devices), else the index."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    return str(local)
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
 
@@ -105,8 +118,8 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu: str):
+        self.gpu = gpu
         self.proc = None
         self.lines = []
 
@@ -364,7 +377,7 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(smi_gpu_id(local)) as clk:
         t0e.record(stream)
         with torch.cuda.stream(stream):
             for k in range(K):
