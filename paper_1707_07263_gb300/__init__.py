@@ -8,7 +8,7 @@ the library is missing.
 """
 from __future__ import annotations
 
-from ._lib import (FFT_ADJOINT, FFT_FORWARD, FFT_INVERSE, FFT_PREC_FP32, FFT_PREC_TC_BF16,  # noqa: F401
+from ._lib import (FFT_ADJOINT, FFT_FORWARD, FFT_INVERSE, FFT_PREC_FP32, FFT_PREC_FP64, FFT_PREC_TC_BF16,  # noqa: F401
                    FFT_PREC_TC_BF16_SPLIT, FFT_PREC_TC_FP16, FFT_PREC_TC_FP16_SPLIT, GbfftError)
 
 

@@ -46,8 +46,10 @@ struct MixedArgs {
   // q = umulhi(n, m) is exact for n * d < 2^32, which every index here meets
   unsigned nb[kMixedMaxPasses], nb_m[kMixedMaxPasses];
   unsigned ns[kMixedMaxPasses], ns_m[kMixedMaxPasses];
+  unsigned tws[kMixedMaxPasses];   // per pass: twiddle stride N / (Ns R) into W_N^m
   int conj_in, scale_out;
   double sx, sy;      // output scale (1/N of Eq. 2 exact to FP64 for the FP64 kernel)
+  float fsx, fsy;     // the same rounded to FP32 for the FP32 kernel
 };
 int mixed_radices(long long N, int* rad);
 int mixed_plan_init(fft_plan* p);

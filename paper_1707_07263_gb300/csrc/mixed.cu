@@ -17,6 +17,8 @@
 // W_{Ns R}^{r k} = W_N^{r k N / (Ns R)}.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include <type_traits>
 
 #include "gbfft_internal.h"
@@ -232,8 +234,15 @@ __device__ __forceinline__ void mixed_pass(const MixedArgs& a, int s, const T* s
   const int N = a.N;
   const unsigned NB = a.nb[s], nbm = a.nb_m[s], Ns = a.ns[s], nsm = a.ns_m[s];
   const int total = a.C * (int)NB;
-  const int stride = N / ((int)Ns * R);
-  const S sx = (S)a.sx, sy = (S)a.sy;   // converted once: no FP64 work in the FP32 kernel
+  const int stride = (int)a.tws[s];
+  S sx, sy;   // the FP32 kernel reads FP32 copies: no FP64 conversion on its path
+  if constexpr (std::is_same_v<T, double2>) {
+    sx = a.sx;
+    sy = a.sy;
+  } else {
+    sx = a.fsx;
+    sy = a.fsy;
+  }
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
     const int c = (int)fdiv((unsigned)b, nbm), j = b - c * (int)NB;
     const bool ok = col0 + c < a.batch;
@@ -347,7 +356,19 @@ int mixed_plan_init(fft_plan* p) {
   const long long N = p->n;
   const bool fp64 = p->prec == FFT_PREC_FP64;
   const size_t esz = fp64 ? 16 : 8;
-  const long long tile = fp64 ? 2048 : 4096;   // points per CTA when several transforms share one
+  // points per CTA when several transforms share one, and the CTA size for
+  // such tiles (GBFFT_MIXED_TILE / GBFFT_MIXED_THREADS override the FP32
+  // values for measurement)
+  long long tile = fp64 ? 2048 : 4096;
+  int small_threads = 256;
+  if (!fp64) {
+    const char* et = getenv("GBFFT_MIXED_TILE");
+    const char* eh = getenv("GBFFT_MIXED_THREADS");
+    const long long t = (et && *et) ? atoll(et) : 0;
+    const int h = (eh && *eh) ? atoi(eh) : 0;
+    if (t >= 256 && t <= 8192) tile = t;
+    if (h == 128 || h == 256 || h == 512) small_threads = h;
+  }
   a.nrad = mixed_radices(N, a.rad);
   if (a.nrad == 0 || N > (fp64 ? kMixedMaxN64 : kMixedMaxN)) return FFT_ERR_UNSUPPORTED;
   a.N = (int)N;
@@ -363,9 +384,10 @@ int mixed_plan_init(fft_plan* p) {
       a.ns[s] = ns;
       a.ns_m[s] = ns == 1 ? 0u : (unsigned)((0x100000000ULL + ns - 1) / ns);
       ns *= (unsigned)a.rad[s];
+      a.tws[s] = (unsigned)(N / ns);
     }
   }
-  p->mixed_threads = a.C * N <= tile ? 256 : 512;
+  p->mixed_threads = a.C * N <= tile ? small_threads : 512;
   // padding pays when a radix-8 or -16 pass leads (its writes are strided by
   // the radix); pure odd-radix lengths keep the unpadded layout
   // (when the padded buffers fit in shared memory)
@@ -404,6 +426,8 @@ int mixed_exec(fft_plan* p, const void* in, void* out, int conj, double sx, doub
   a.scale_out = scale_out;
   a.sx = sx;
   a.sy = sy;
+  a.fsx = (float)sx;
+  a.fsy = (float)sy;
   const long long tiles = (p->batch + a.C - 1) / a.C;
   if (tiles > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
   void* args[] = {(void*)&a};
