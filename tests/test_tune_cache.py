@@ -1,0 +1,74 @@
+"""Host logic of the autotune cache (no GPU): the shipped GB300 results are
+well-formed plan configurations, and a lookup takes the user's cache first,
+then the shipped file, and only then runs (and stores) a new search."""
+from __future__ import annotations
+
+import json
+import os
+
+import pytest
+
+from paper_1707_07263_gb300 import _lib, tune
+
+
+def test_shipped_entries_are_well_formed():
+    shipped = json.load(open(tune.SHIPPED))
+    fields = [name for name, _ in _lib.FftPlanConfig._fields_]
+    assert shipped
+    for k, v in shipped.items():
+        dev, n, batch, prec = k.split("|")
+        n, batch, prec = int(n[2:]), int(batch[6:]), int(prec[5:])
+        lg = n.bit_length() - 1
+        assert dev and n == 1 << lg and batch >= 1 and prec == _lib.FFT_PREC_FP32, k
+        c = v["config"]
+        assert sorted(c) == sorted(fields), k
+        assert v["us"] > 0
+        assert c["tma"] in (-1, 0, 1, 2) and c["fused"] in (-1, 0, 1) and c["halves"] in (0, 1, 2)
+        if c["npass"] == 1:
+            assert c["lg1"] == lg <= 14, k
+        elif c["npass"] == 2:
+            assert c["lg1"] + c["lg2"] == lg and c["c1"] >= 1 and c["c2"] >= 1, k
+        else:
+            assert c["npass"] == 3 and 0 < c["lg1"] + c["lg2"] < lg and min(c["c1"], c["c2"], c["c3"]) >= 1, k
+        assert _lib.FftPlanConfig.from_dict(c).as_dict() == c
+
+
+@pytest.fixture
+def fake_tuner(tmp_path, monkeypatch):
+    calls = []
+    monkeypatch.setenv("GBFFT_TUNE_CACHE", str(tmp_path / "cache" / "tune.json"))
+    shipped = tmp_path / "shipped.json"
+    shipped.write_text(json.dumps({"dev|n=64|batch=8|prec=0": {"config": {"npass": 1, "lg1": 6}, "us": 1.0}}))
+    monkeypatch.setattr(tune, "SHIPPED", str(shipped))
+    monkeypatch.setattr(tune, "key", lambda n, batch, prec, device: f"dev|n={n}|batch={batch}|prec={prec}")
+
+    def autotune(n, batch, prec, device):
+        calls.append((n, batch, prec))
+        return {"npass": 1, "lg1": n.bit_length() - 1, "tma": len(calls)}, 2.0
+
+    monkeypatch.setattr(tune, "autotune", autotune)
+    return calls
+
+
+def test_lookup_order(fake_tuner):
+    calls = fake_tuner
+    assert tune.tuned_config(64, 8, 0, device="cpu") == {"npass": 1, "lg1": 6}   # shipped
+    assert calls == [] and not os.path.exists(tune.cache_path())
+    cfg = tune.tuned_config(128, 8, 0, device="cpu")                            # neither: search
+    assert calls == [(128, 8, 0)] and cfg["tma"] == 1
+    stored = json.load(open(tune.cache_path()))
+    assert stored["dev|n=128|batch=8|prec=0"]["config"] == cfg
+    assert tune.tuned_config(128, 8, 0, device="cpu") == cfg and len(calls) == 1  # cached
+    cfg2 = tune.tuned_config(64, 8, 0, device="cpu", retune=True)               # forced search
+    assert len(calls) == 2 and cfg2["tma"] == 2
+    assert tune.tuned_config(64, 8, 0, device="cpu") == cfg2                   # user cache before shipped
+    assert os.listdir(os.path.dirname(tune.cache_path())) == ["tune.json"]    # no temporary left
+
+
+def test_corrupt_cache_is_replaced(fake_tuner):
+    path = tune.cache_path()
+    os.makedirs(os.path.dirname(path))
+    open(path, "w").write("{not json")
+    cfg = tune.tuned_config(256, 2, 0, device="cpu")
+    assert fake_tuner == [(256, 2, 0)]
+    assert json.load(open(path)) == {"dev|n=256|batch=2|prec=0": {"config": cfg, "us": 2.0}}
