@@ -43,7 +43,7 @@ def _stream_handle(stream=None) -> int:
 
 class Plan:
     """Owns one library plan and (for four-step plans) its torch-allocated
-    workspace.  ``kind`` is "1d", "2d" or "many"."""
+    workspace.  ``kind`` is "1d", "2d", "many" or "r2c" (real data)."""
 
     def __init__(self, kind: str, shape, batch: int = 1, dir: int = FORWARD, prec="fp32",
                  device=None, lengths=None, config: dict | None = None):
@@ -54,6 +54,8 @@ class Plan:
         self.dir = int(dir)
         self.prec = _prec_code(prec)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             if kind == "1d" and config is not None:
                 cfg = L.FftPlanConfig.from_dict(config)
@@ -97,14 +99,30 @@ class Plan:
                                    ctypes.c_void_p(_stream_handle(stream)))
         L.check(rc, "fft_exec")
 
+    def numel(self) -> int:
+        """Complex elements one execution reads and writes."""
+        if self.kind == "many":
+            return sum(self.lengths)
+        m = self.batch
+        for d in self.shape:
+            m *= int(d)
+        return m
+
     def __call__(self, x: torch.Tensor, out: torch.Tensor | None = None, dir: int | None = None,
                  stream=None) -> torch.Tensor:
+        if self.kind == "r2c":
+            raise TypeError("real plans run through rfft / irfft")
         want = torch.complex128 if self.prec == L.FFT_PREC_FP64 else torch.complex64
-        if x.dtype != want or not x.is_cuda:
-            raise TypeError(f"expected a {want} CUDA tensor")
+        if x.dtype != want or not x.is_cuda or x.device != self.device:
+            raise TypeError(f"expected a {want} tensor on {self.device}")
+        if x.numel() != self.numel():
+            raise ValueError(f"expected {self.numel()} elements, got {x.numel()}")
         x = x.contiguous()
         if out is None:
             out = torch.empty_like(x)
+        elif (out.dtype != want or out.device != self.device or out.numel() != x.numel()
+              or not out.is_contiguous()):
+            raise ValueError("out must be a contiguous tensor of the input's dtype, device and size")
         self.exec_ptr(x.data_ptr(), out.data_ptr(), dir, stream)
         return out
 
@@ -173,29 +191,37 @@ class _FFT1d(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, dir, prec):
         n = x.shape[-1]
-        batch = x.numel() // n if n else 0
-        plan = get_plan("1d", (n,), batch, prec, x.device)
-        ctx.plan, ctx.dir = plan, dir
-        y = plan(x, dir=dir)
-        return y
+        ctx.dir = dir
+        ctx.plan = None
+        if x.numel() == 0 and n > 0:   # no rows: nothing to transform
+            return torch.empty_like(x)
+        plan = get_plan("1d", (n,), x.numel() // n if n else 0, prec, x.device)
+        ctx.plan = plan
+        return plan(x, dir=dir)
 
     @staticmethod
     def backward(ctx, g):
-        g = g.contiguous()
-        return ctx.plan(g, dir=ctx.dir ^ ADJOINT), None, None
+        if ctx.plan is None:
+            return torch.zeros_like(g), None, None
+        return ctx.plan(g.contiguous(), dir=ctx.dir ^ ADJOINT), None, None
 
 
 class _FFT2d(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, dir, prec):
         ny, nx = x.shape[-2], x.shape[-1]
-        batch = x.numel() // (ny * nx)
-        plan = get_plan("2d", (ny, nx), batch, prec, x.device)
-        ctx.plan, ctx.dir = plan, dir
+        ctx.dir = dir
+        ctx.plan = None
+        if x.numel() == 0 and ny * nx > 0:
+            return torch.empty_like(x)
+        plan = get_plan("2d", (ny, nx), x.numel() // (ny * nx) if ny * nx else 0, prec, x.device)
+        ctx.plan = plan
         return plan(x, dir=dir)
 
     @staticmethod
     def backward(ctx, g):
+        if ctx.plan is None:
+            return torch.zeros_like(g), None, None
         return ctx.plan(g.contiguous(), dir=ctx.dir ^ ADJOINT), None, None
 
 
@@ -251,6 +277,8 @@ def fft_many(packed: torch.Tensor, lengths, inverse: bool = False, prec="fp32") 
     lengths = [int(v) for v in lengths]
     if packed.numel() != sum(lengths):
         raise ValueError("packed size does not match the sum of the lengths")
+    if not lengths:
+        return packed.reshape(-1).clone()
     return _FFTMany.apply(packed.reshape(-1), lengths, INVERSE if inverse else FORWARD, prec)
 
 
