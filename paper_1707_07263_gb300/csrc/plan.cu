@@ -9,6 +9,8 @@
 //               W_N^{n2*k1}, written to the workspace as Y[k1][n2];
 //       pass 2  row FFTs of length N2 of Y[k1][.], written transposed to
 //               X[k1 + N1*k2].
+//     From 2^22 the row length N2 is itself split once more (three passes,
+//     N = N1*N2*N3), so that every pass's sub-FFT stays at most 2^12 points.
 //   * 2-D ny x nx: row FFTs, then column FFTs in place (Sec. 2.3.2: rows,
 //     then columns).
 #include <cuda_runtime.h>
@@ -488,11 +490,12 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
   return rc;
 }
 
-// Planner for 1-D lengths: kind, split and kernel variants.
-// Planner for 1-D lengths.  cfg fields <= 0 (or tma < 0) take the defaults:
-// one on-chip pass up to 2^14 (TMA-staged for 2^9..2^12), two passes up to
-// 2^22, three passes above; split lengths as even as possible; as many
-// adjacent columns per CTA as fit 2^13 points (at most 16).
+// Planner for 1-D lengths: kind, split and kernel variants.  cfg fields <= 0
+// (or tma < 0) take the defaults: one on-chip pass up to 2^14 (TMA-staged for
+// 2^9..2^11, persistent with an L2 prefetch at 2^14), two passes
+// below 2^22 (2^8-point column tiles from 2^16 to 2^20, else the even split),
+// three passes 2^8 * 2^8 * rest from 2^22; as many adjacent columns per CTA
+// as fit 2^13 points (at most 16).
 static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   fft_plan_config dflt;
   memset(&dflt, 0, sizeof(dflt));
