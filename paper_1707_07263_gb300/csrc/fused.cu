@@ -9,9 +9,10 @@
 //     A(0), A(1) B(0), A(2) B(1), ..., A(S-1) B(S-2), B(S-1)
 // A(s) = column tiles of slab s (input -> slot s mod R, with the W_N twiddle),
 // B(s) = row tiles of slab s (slot -> output, transposed).  A slot is rewritten
-// only after the row tiles that read it are done, so the 2 x 16 MB of
-// workspace (3 x 16 MB) stays resident in the 126 MB L2 while inputs and outputs stream
-// with evict-first hints: DRAM sees roughly one read and one write per point.
+// only after the row tiles that read it are done, so the 3 x 16 MB of
+// workspace stays resident in L2 (about 126 MB usable) while inputs and
+// outputs stream with evict-first hints: DRAM sees roughly one read and one
+// write per point.
 // With three slots, A(s) waits for B(s-3), which sits a whole group of items
 // earlier in the sequence, so CTAs working through the sequence in order do
 // not stall on work dispatched just before them.

@@ -1,8 +1,10 @@
 // twiddle.cu -- device-side generation of the twiddle look-up tables
 // (paper Sec. 2.3.1: the sine/cosine values are computed once, before the FFT,
 // and kept in a table the butterflies read).  Every entry is evaluated in FP64
-// with sincospi on an exactly representable argument -2m/M (M a power of two,
-// the exponent m reduced mod M by Eq. 3) and rounded once to FP32.
+// with sincospi of -2m/M, the exponent m reduced mod M first (Eq. 3), and
+// rounded once to FP32 (kept in FP64 for FP64 transforms).  For M a power of
+// two the argument -2m/M is exact; for the mixed-radix lengths it carries one
+// FP64 rounding (relative 2^-53), far below either table precision.
 #include <cuda_runtime.h>
 
 #include "gbfft_internal.h"
