@@ -82,7 +82,7 @@ MUTATIONS = {
     "butterfly_sign": ("y[2 * (h + k)] = er - tr;", "y[2 * (h + k)] = er + tr;"),
     "butterfly_index": ("oracle_w(k, n, s, &wr, &wi);", "oracle_w(k, h, s, &wr, &wi);"),
     "no_inverse_scale": ("return dir == 1 ? 1.0 / (double)n : 1.0;", "return 1.0;"),
-    "transposed_2d": ("col[2 * y] = out[2 * (y * nx + x)];", "col[2 * y] = out[2 * (x * nx + y)];"),
+    "transposed_2d": ("col[2 * y] = out[2 * (y * nx + x)];", "col[2 * y] = out[2 * (x * ny + y)];"),  # in bounds
     "swapped_halves": ("fft_rec(h, x, 2 * stride, y, s);", "fft_rec(h, x + 2 * stride, 2 * stride, y, s);"),
 }
 
