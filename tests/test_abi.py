@@ -21,7 +21,8 @@ def lib():
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    with open(HEADER) as f:
+        src = f.read()
     return sorted(set(re.findall(r"GBFFT_API\s+[\w\s\*]+?\b(fft_\w+)\s*\(", src)))
 
 

@@ -88,7 +88,8 @@ MUTATIONS = {
 
 
 def _mutated_lib(tmpdir, name, old, new):
-    src = open(os.path.join(os.path.dirname(oracle.__file__), "fft_oracle.c")).read()
+    with open(os.path.join(os.path.dirname(oracle.__file__), "fft_oracle.c")) as f:
+        src = f.read()
     assert old in src, f"mutation {name}: anchor not found"
     path = os.path.join(tmpdir, f"{name}.c")
     with open(path, "w") as f:

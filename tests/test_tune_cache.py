@@ -11,8 +11,13 @@ import pytest
 from paper_1707_07263_gb300 import _lib, tune
 
 
+def _read_json(path):
+    with open(path) as f:
+        return json.load(f)
+
+
 def test_shipped_entries_are_well_formed():
-    shipped = json.load(open(tune.SHIPPED))
+    shipped = _read_json(tune.SHIPPED)
     fields = [name for name, _ in _lib.FftPlanConfig._fields_]
     assert shipped
     for k, v in shipped.items():
@@ -56,7 +61,7 @@ def test_lookup_order(fake_tuner):
     assert calls == [] and not os.path.exists(tune.cache_path())
     cfg = tune.tuned_config(128, 8, 0, device="cpu")                            # neither: search
     assert calls == [(128, 8, 0)] and cfg["tma"] == 1
-    stored = json.load(open(tune.cache_path()))
+    stored = _read_json(tune.cache_path())
     assert stored["dev|n=128|batch=8|prec=0"]["config"] == cfg
     assert tune.tuned_config(128, 8, 0, device="cpu") == cfg and len(calls) == 1  # cached
     cfg2 = tune.tuned_config(64, 8, 0, device="cpu", retune=True)               # forced search
@@ -68,7 +73,8 @@ def test_lookup_order(fake_tuner):
 def test_corrupt_cache_is_replaced(fake_tuner):
     path = tune.cache_path()
     os.makedirs(os.path.dirname(path))
-    open(path, "w").write("{not json")
+    with open(path, "w") as f:
+        f.write("{not json")
     cfg = tune.tuned_config(256, 2, 0, device="cpu")
     assert fake_tuner == [(256, 2, 0)]
-    assert json.load(open(path)) == {"dev|n=256|batch=2|prec=0": {"config": cfg, "us": 2.0}}
+    assert _read_json(path) == {"dev|n=256|batch=2|prec=0": {"config": cfg, "us": 2.0}}
