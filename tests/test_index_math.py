@@ -1,0 +1,54 @@
+"""Host-side checks of two index identities the kernels rely on (no GPU).
+
+1. The padded shared-memory index pidx(n) = n + floor(n/16) of the on-chip
+   Stockham passes splits as pidx(base + d) = pidx(base) + pidx(d) for every
+   butterfly's element offsets (reads d = r L/R from base j, writes d = q Ns
+   from base (j div Ns) Ns R + (j mod Ns)), in the forward radix schedule
+   (remainder pass first) and the reversed one (remainder last).  The kernels
+   address each butterfly's elements as one base register plus constants on
+   the strength of it.
+2. The mixed-radix kernel divides by run-time d with q = floor(n m / 2^32),
+   m = ceil(2^32 / d); that equals floor(n / d) for every divisor d and index
+   n the kernel can meet (d, n < 2^14 + 1024)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+
+def pidx(n):
+    return n + (n >> 4)
+
+
+def schedule(lg: int, rev: bool):
+    """log2 of the radices, pass by pass: 16s plus one 2/4/8 remainder."""
+    rest = [4] * (lg // 4)
+    if lg % 4:
+        rest = rest + [lg % 4] if rev else [lg % 4] + rest
+    return rest
+
+
+@pytest.mark.parametrize("rev", [False, True])
+@pytest.mark.parametrize("lg", range(1, 15))
+def test_padded_index_splits(lg, rev):
+    L = 1 << lg
+    lgns = 0
+    for lgr in schedule(lg, rev):
+        R, Ns = 1 << lgr, 1 << lgns
+        j = np.arange(L // R)
+        r = np.arange(R)[:, None]
+        d_read = r * (L // R)
+        assert np.array_equal(pidx(j + d_read), pidx(j) + pidx(d_read)), ("read", lg, rev, R, Ns)
+        base = (j // Ns) * Ns * R + (j % Ns)
+        d_write = r * Ns
+        assert np.array_equal(pidx(base + d_write), pidx(base) + pidx(d_write)), ("write", lg, rev, R, Ns)
+        lgns += lgr
+    assert lgns == lg
+
+
+def test_reciprocal_division_is_exact():
+    n = np.arange(0, (1 << 14) + 1024, dtype=np.uint64)
+    for d in range(2, (1 << 14) + 1):
+        m = np.uint64(((1 << 32) + d - 1) // d)
+        q = (n * m) >> np.uint64(32)
+        assert np.array_equal(q, n // np.uint64(d)), d
