@@ -480,18 +480,34 @@ class HostPipeline:
         direct = self.full_plan is not None and self.usable(xf) and self.usable(of)
         if self.want_direct and not direct:
             raise ValueError("direct mode needs page-locked host buffers the GPU can address")
-        for s in self.streams:
-            s.wait_stream(cur)
         if direct:
+            # one launch sequence on the transform stream; the download stream
+            # (which join=False callers join) is ordered after it
             self.last_mode = "direct"
+            self.s_fft.wait_stream(cur)
             self.full_plan.exec_ptr(xf.data_ptr(), of.data_ptr(), self.dir, self.s_fft)
             self.s_d2h.wait_stream(self.s_fft)
-            self.s_h2d.wait_stream(self.s_fft)
             if join:
                 cur.wait_stream(self.s_d2h)
             return out_host
         self.last_mode = "copy"
         self._copy_setup()
+        if self.nchunks == 1:
+            # nothing to overlap: upload, transform and download in order on
+            # the transform stream, with no cross-stream events
+            m = self.batch * self.n
+            s = self.s_fft
+            s.wait_stream(cur)
+            with torch.cuda.stream(s):
+                self.dev_in[0][:m].copy_(xf, non_blocking=True)
+                self.plan.exec_ptr(self.dev_in[0].data_ptr(), self.dev_out[0].data_ptr(), self.dir, s)
+                of.copy_(self.dev_out[0][:m], non_blocking=True)
+            self.s_d2h.wait_stream(s)
+            if join:
+                cur.wait_stream(self.s_d2h)
+            return out_host
+        for s in self.streams:
+            s.wait_stream(cur)
         uploaded = [None, None]
         transformed = [None, None]
         downloaded = [None, None]
