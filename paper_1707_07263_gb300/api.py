@@ -410,7 +410,9 @@ class HostPipeline:
     copy    the batch is cut into chunks and three CUDA streams overlap the
             upload of chunk i+1, the transform of chunk i and the download of
             chunk i-1, events ordering each chunk's steps; two device buffers
-            per stage, allocated on first use.
+            per stage, allocated on first use.  A batch that fits one chunk
+            runs its three steps in order on the transform stream (nothing to
+            overlap, no events).
 
     direct=None picks direct for one-pass plans when both buffers are usable
     and copy otherwise; True / False force one (True raises if a buffer is not
