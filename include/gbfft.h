@@ -1,5 +1,6 @@
 /*
- * gbfft.h -- C ABI of the GB300 (sm_103a) power-of-two complex FFT library.
+ * gbfft.h -- C ABI of the GB300 (sm_103a) complex FFT library: power-of-two
+ * lengths (1-D, 2-D, uneven batches, real data) and 7-smooth lengths.
  *
  * What the library computes (paper Sec. 2.1):
  *   forward  (Eq. 1):  X(k) = sum_{n=0}^{N-1} x(n) W_N^{nk},            W_N = exp(-2*pi*i/N)
@@ -8,11 +9,15 @@
  * Outputs are in natural order.  Data are complex64: interleaved (re, im)
  * float32 pairs, contiguous; a batch of B transforms of length N is B*N
  * complex values with transform b at offset b*N.  2-D images are row-major
- * (element (y, x) at y*nx + x).
+ * (element (y, x) at y*nx + x).  FFT_PREC_FP64 plans take complex128 (re, im
+ * double pairs) instead; real-data plans (fft_plan_create_r2c) take rows of
+ * float32 and give rows of n/2 + 1 complex64.
  *
- * Memory: every data pointer passed to fft_exec* is a DEVICE pointer owned by
- * the caller, at least 8-byte aligned (FFT_ERR_ALIGN otherwise).  in == out
- * (in place) is allowed for every plan kind.  The library allocates only at
+ * Memory: every data pointer passed to fft_exec* is owned by the caller and
+ * is device memory, or page-locked host memory the device can address
+ * (fft_pointer_usable), at least 8-byte aligned (16 for FFT_PREC_FP64;
+ * FFT_ERR_ALIGN otherwise).  in == out (in place) is allowed for every plan
+ * kind except real-data plans.  The library allocates only at
  * plan creation (the twiddle tables) and in fft_plan_set_workspace(plan, NULL);
  * fft_exec* never allocates, never synchronises the stream and is safe to
  * capture into a CUDA graph.
