@@ -25,7 +25,8 @@
  * Errors: calls return 0 (FFT_OK) or a negative FFT_ERR_* code; plan
  * constructors return NULL on error.  The code of the last failing call on
  * the calling host thread is kept in fft_last_error().  Argument errors are
- * detected on the host before anything is launched.
+ * detected on the host before anything is launched, including plan pointers
+ * that are not live plans (see fft_destroy).
  */
 #ifndef GBFFT_H
 #define GBFFT_H
@@ -209,7 +210,10 @@ GBFFT_API int fft_autotune(int64_t n, int64_t batch, int prec, void* in, void* o
                            void* stream, int iters, fft_plan_config* best, float* best_us);
 
 /* Frees the plan and everything the library allocated for it.  NULL-safe.
- * The caller must not use the plan afterwards. */
+ * The library keeps a record of the plans it has handed out: a pointer that
+ * is not a live plan (never returned by a constructor, or destroyed already)
+ * frees nothing here and sets FFT_ERR_INVALID_ARG, and every other call
+ * rejects it with FFT_ERR_INVALID_ARG (or 0 / -1 from the queries). */
 GBFFT_API void fft_destroy(fft_plan* plan);
 
 /* Bytes of device workspace fft_exec needs (0 for single-pass and 2-D plans). */

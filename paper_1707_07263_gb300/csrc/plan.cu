@@ -19,7 +19,9 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_set>
 
 #include "gbfft_internal.h"
 #include "tile_registry.h"
@@ -918,6 +920,42 @@ static int build_2d(fft_plan* p, int ly, int lx) {
 // ============================================================================
 // C ABI
 // ============================================================================
+// ---- live plan handles -------------------------------------------------------
+// Every plan handed to a caller is recorded until fft_destroy; the entry
+// points reject any other pointer (never created, or already destroyed) with
+// FFT_ERR_INVALID_ARG instead of reading freed memory.  The set and its lock
+// are never destroyed, so calls made while the process exits stay valid.
+static std::mutex& live_mutex() {
+  static std::mutex* m = new std::mutex;
+  return *m;
+}
+static std::unordered_set<const fft_plan*>& live_plans() {
+  static auto* s = new std::unordered_set<const fft_plan*>;
+  return *s;
+}
+static fft_plan* publish(fft_plan* p) {
+  if (!p) return nullptr;
+  try {
+    std::lock_guard<std::mutex> g(live_mutex());
+    live_plans().insert(p);
+  } catch (...) {
+    free_plan(p);
+    set_err(FFT_ERR_ALLOC);
+    return nullptr;
+  }
+  return p;
+}
+static bool is_live(const fft_plan* p) {
+  if (!p) return false;
+  std::lock_guard<std::mutex> g(live_mutex());
+  return live_plans().count(p) != 0;
+}
+static bool retire(const fft_plan* p) {
+  if (!p) return false;
+  std::lock_guard<std::mutex> g(live_mutex());
+  return live_plans().erase(p) != 0;
+}
+
 extern "C" {
 
 // Lengths that are not powers of two (7-smooth N <= kMixedMaxN, FP32), and
@@ -998,7 +1036,7 @@ static fft_plan* create_1d(int64_t n, int64_t batch, int dir, int prec, const ff
 }
 
 fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec) {
-  return create_1d(n, batch, dir, prec, nullptr);
+  return publish(create_1d(n, batch, dir, prec, nullptr));
 }
 
 static int plan_real(fft_plan* p, int lgN) {
@@ -1064,15 +1102,15 @@ fft_plan* fft_plan_create_r2c(int64_t n, int64_t batch, int prec) {
     set_err(rc);
     return nullptr;
   }
-  return p;
+  return publish(p);
 }
 
 fft_plan* fft_plan_create_config(int64_t n, int64_t batch, int dir, int prec, const fft_plan_config* cfg) {
-  return create_1d(n, batch, dir, prec, cfg);
+  return publish(create_1d(n, batch, dir, prec, cfg));
 }
 
 int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
-  if (!p || !out) return set_err(FFT_ERR_INVALID_ARG);
+  if (!is_live(p) || !out) return set_err(FFT_ERR_INVALID_ARG);
   memset(out, 0, sizeof(*out));
   out->tma = -1;
   out->fused = 0;
@@ -1138,7 +1176,7 @@ fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int
     set_err(rc);
     return nullptr;
   }
-  return p;
+  return publish(p);
 }
 
 fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, int prec) {
@@ -1170,20 +1208,21 @@ fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, i
     set_err(rc);
     return nullptr;
   }
-  return p;
+  return publish(p);
 }
 
 int fft_exec(fft_plan* plan, const void* in, void* out, void* stream) {
-  if (!plan) return set_err(FFT_ERR_INVALID_ARG);
+  if (!is_live(plan)) return set_err(FFT_ERR_INVALID_ARG);
   return set_err(exec_plan(plan, in, out, plan->dir, (cudaStream_t)stream));
 }
 
 int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* stream) {
+  if (!is_live(plan)) return set_err(FFT_ERR_INVALID_ARG);
   return set_err(exec_plan(plan, in, out, dir, (cudaStream_t)stream));
 }
 
 int fft_exec_filter(fft_plan* plan, const void* in, void* out, const void* filt, void* stream) {
-  if (!plan || !in || !out || !filt) return set_err(FFT_ERR_INVALID_ARG);
+  if (!is_live(plan) || !in || !out || !filt) return set_err(FFT_ERR_INVALID_ARG);
   if (((uintptr_t)in & 7) || ((uintptr_t)out & 7) || ((uintptr_t)filt & 7)) return set_err(FFT_ERR_ALIGN);
   int rc = exec_filter_plan(plan, (const float2*)in, (float2*)out, (const float2*)filt, (cudaStream_t)stream);
   if (rc == FFT_OK && cudaPeekAtLastError() != cudaSuccess) {
@@ -1193,9 +1232,14 @@ int fft_exec_filter(fft_plan* plan, const void* in, void* out, const void* filt,
   return set_err(rc);
 }
 
-void fft_destroy(fft_plan* plan) { free_plan(plan); }
+void fft_destroy(fft_plan* plan) {
+  if (retire(plan))
+    free_plan(plan);
+  else if (plan)
+    set_err(FFT_ERR_INVALID_ARG);   // not a live plan (e.g. destroyed twice): nothing is freed
+}
 
-size_t fft_plan_workspace_bytes(const fft_plan* plan) { return plan ? plan->ws_bytes : 0; }
+size_t fft_plan_workspace_bytes(const fft_plan* plan) { return is_live(plan) ? plan->ws_bytes : 0; }
 
 // A real-data plan hands the front of its workspace to its complex plan and
 // keeps the rest for Z.
@@ -1208,7 +1252,7 @@ static void distribute_real_ws(fft_plan* plan) {
 }
 
 int fft_plan_set_workspace(fft_plan* plan, void* dev_ptr) {
-  if (!plan) return set_err(FFT_ERR_INVALID_ARG);
+  if (!is_live(plan)) return set_err(FFT_ERR_INVALID_ARG);
   if (dev_ptr && ((uintptr_t)dev_ptr & 255)) return set_err(FFT_ERR_ALIGN);
   if (plan->ws_owned && plan->ws) cudaFree(plan->ws);
   plan->ws = nullptr;
@@ -1229,13 +1273,13 @@ int fft_plan_set_workspace(fft_plan* plan, void* dev_ptr) {
   return FFT_OK;
 }
 
-int64_t fft_plan_length(const fft_plan* plan) { return plan ? plan->n : 0; }
-int64_t fft_plan_batch(const fft_plan* plan) { return plan ? plan->batch : 0; }
-int fft_plan_launches(const fft_plan* plan) { return plan ? plan->launches : 0; }
-int fft_plan_kind(const fft_plan* plan) { return plan ? plan->kind : -1; }
+int64_t fft_plan_length(const fft_plan* plan) { return is_live(plan) ? plan->n : 0; }
+int64_t fft_plan_batch(const fft_plan* plan) { return is_live(plan) ? plan->batch : 0; }
+int fft_plan_launches(const fft_plan* plan) { return is_live(plan) ? plan->launches : 0; }
+int fft_plan_kind(const fft_plan* plan) { return is_live(plan) ? plan->kind : -1; }
 
 int fft_plan_describe(const fft_plan* p, char* buf, size_t len) {
-  if (!p || !buf || len == 0) return set_err(FFT_ERR_INVALID_ARG);
+  if (!is_live(p) || !buf || len == 0) return set_err(FFT_ERR_INVALID_ARG);
   static const char* kinds[] = {"single", "fourstep", "2d", "many", "real", "mixed", "?", "?"};
   snprintf(buf, len,
            "kind=%s n=%lld batch=%lld lg1=%d lg2=%d c1=%d c2=%d threads1=%d smem1=%d threads2=%d smem2=%d "
@@ -1247,7 +1291,7 @@ int fft_plan_describe(const fft_plan* p, char* buf, size_t len) {
 }
 
 int fft_status(fft_plan* plan, void* stream) {
-  if (!plan || !plan->d_status) return set_err(FFT_ERR_INVALID_ARG);
+  if (!is_live(plan) || !plan->d_status) return set_err(FFT_ERR_INVALID_ARG);
   int h = 0;
   if (cudaMemcpyAsync(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
     return set_err(FFT_ERR_CUDA);

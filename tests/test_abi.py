@@ -182,3 +182,26 @@ def test_fp64_and_mixed_length_limits(lib):
     assert lib.fft_last_error() == -6
     assert lib.fft_plan_create_r2c(16, 1, fp64) is None
     assert lib.fft_last_error() == -6
+
+
+def test_pointers_that_are_not_live_plans(lib):
+    """A pointer that no plan constructor returned (or one already destroyed)
+    is refused by every entry point, and destroying it frees nothing."""
+    from paper_1707_07263_gb300 import _lib
+    fake_buf = ctypes.create_string_buffer(4096)
+    fake = ctypes.c_void_p(ctypes.addressof(fake_buf))
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.fft_exec(fake, p, p, None) == -1
+    assert lib.fft_exec_dir(fake, p, p, 0, None) == -1
+    assert lib.fft_exec_filter(fake, p, p, p, None) == -1
+    assert lib.fft_plan_set_workspace(fake, None) == -1
+    assert lib.fft_status(fake, None) == -1
+    assert lib.fft_plan_workspace_bytes(fake) == 0 and lib.fft_plan_launches(fake) == 0
+    assert lib.fft_plan_length(fake) == 0 and lib.fft_plan_batch(fake) == 0 and lib.fft_plan_kind(fake) == -1
+    assert lib.fft_plan_get_config(fake, ctypes.byref(_lib.FftPlanConfig())) == -1
+    assert lib.fft_plan_describe(fake, buf, 64) == -1
+    lib.fft_destroy(fake)
+    assert lib.fft_last_error() == -1
+    lib.fft_destroy(fake)                       # twice: still nothing freed
+    assert fake_buf.raw == bytes(4096)
