@@ -93,7 +93,8 @@ enum {
  * on-chip pass per transform (Sec. 2.3.2: short data is not partitioned);
  * longer ones are split N = N1*N2 into a column pass with twiddle scaling and
  * a row pass through global memory (Sec. 2.3.2: two exchanges between shared
- * and global memory).
+ * and global memory); from 2^22 the rows are split once more (three passes).
+ * Multi-pass plans need a workspace (fft_plan_workspace_bytes).
  * Builds the twiddle tables on the current device (FP64 sincospi rounded
  * once to FP32; Sec. 2.3.1 look-up table).  Returns NULL on error. */
 GBFFT_API fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec);
@@ -126,8 +127,13 @@ GBFFT_API fft_plan* fft_plan_create_r2c(int64_t n, int64_t batch, int prec);
  * the lengths before it.  The host array is copied; the caller keeps it. */
 GBFFT_API fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, int prec);
 
-/* Runs the plan on `stream` (a cudaStream_t; NULL = legacy default stream).
- * Asynchronous.  in/out: device pointers to the packed complex64 data. */
+/* Runs the plan on `stream` (a cudaStream_t; NULL = legacy default stream)
+ * in the plan's direction.  Asynchronous: returns once the launches are
+ * queued.  in/out: the packed data (complex64; complex128 for FFT_PREC_FP64;
+ * see fft_plan_create_r2c for real-data plans) in device memory or in memory
+ * fft_pointer_usable accepts.  FFT_ERR_NO_WORKSPACE if a multi-pass plan has
+ * no workspace; a bounded device-side wait that ran out shows later in
+ * fft_status, not here. */
 GBFFT_API int fft_exec(fft_plan* plan, const void* in, void* out, void* stream);
 
 /* As fft_exec, with an explicit direction instead of the plan's (the twiddle
