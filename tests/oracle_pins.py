@@ -4,7 +4,8 @@ Each check takes the oracle's compiled library (so the mutation test can run
 the same battery against deliberately broken copies) and raises
 AssertionError on failure.  Sources of truth, none of them the oracle:
 
-* hand-worked values from Eq. 1 / Eq. 2 (tests/golden/dft_worked_examples.txt);
+* hand-worked values from Eq. 1 / Eq. 2 (tests/golden/dft_worked_examples.txt,
+  and mixed_length_worked_examples.txt for N = 3, 5, 6);
 * the N=2 butterfly and the N=4 DFT matrix written out by hand;
 * closed forms: delta, shifted delta, single tone, constant, cosine;
 * invariants: Parseval, linearity, inverse round trip, Hermitian symmetry of
@@ -41,10 +42,10 @@ def _close(got, ref, tol, what):
     assert err <= tol, f"{what}: relative error {err:.3e} > {tol:.1e}"
 
 
-def load_golden():
+def load_golden(path=GOLDEN):
     cases = []
     cur = None
-    with open(GOLDEN) as f:
+    with open(path) as f:
         for line in f:
             line = line.strip()
             if not line or line.startswith("#"):
@@ -65,6 +66,23 @@ def check_golden(lib):
     for c in load_golden():
         d = oracle.FORWARD if c["dir"] == "fwd" else oracle.INVERSE
         for fn in (oracle.dft, oracle.fft):
+            got = fn(c["in"], d, lib=lib)
+            assert np.max(np.abs(got - c["out"])) <= 1e-12 * max(1.0, np.max(np.abs(c["out"]))), \
+                f"golden {c['name']} via {fn.__name__}: {got} vs {c['out']}"
+
+
+GOLDEN_MIXED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                            "mixed_length_worked_examples.txt")
+
+
+def check_golden_mixed(lib):
+    """Hand-worked examples at N = 3, 5, 6 through the O(N^2) sum and the
+    oracle's default route (which sends such lengths to that sum)."""
+    cases = load_golden(GOLDEN_MIXED)
+    assert {c["n"] for c in cases} == {3, 5, 6}
+    for c in cases:
+        d = oracle.FORWARD if c["dir"] == "fwd" else oracle.INVERSE
+        for fn in (oracle.dft, oracle.transform):
             got = fn(c["in"], d, lib=lib)
             assert np.max(np.abs(got - c["out"])) <= 1e-12 * max(1.0, np.max(np.abs(c["out"]))), \
                 f"golden {c['name']} via {fn.__name__}: {got} vs {c['out']}"
@@ -323,4 +341,4 @@ def check_mixed_lengths(lib):
 
 ALL_CHECKS = (check_golden, check_small_by_hand, check_closed_forms, check_invariants,
               check_dft_vs_fft, check_numpy, check_fft2, check_range_compress, check_real_transforms,
-              check_mixed_lengths, check_golden_real_and_filter)
+              check_mixed_lengths, check_golden_real_and_filter, check_golden_mixed)
