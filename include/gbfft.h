@@ -254,12 +254,18 @@ GBFFT_API int fft_status(fft_plan* plan, void* stream);
  *           anything larger returns FFT_ERR_INVALID_ARG without launching.
  *   dir:    as fft_exec_dir.  in/out: caller-owned device pointers (8-byte
  *           aligned, in == out allowed).  stream: cudaStream_t or NULL.
- * Nothing is allocated: the workspace (32 MiB) and the twiddle tables live in a
- * static device array inside the library, reserved on every GPU that loads it
- * until the process exits.  The first call on a device looks up that array's
- * device address (and raises the kernels' shared-memory limit) once; make that
- * first call before any stream capture.  All calls share the array: calls
- * whose work overlaps on the GPU race on it, so serialise them. */
+ * Nothing is allocated per call: the workspace (32 MiB) and the twiddle tables
+ * live in a static device array inside the library.  The CUDA runtime loads a
+ * library's device code, and with it this array, onto a device the first time
+ * the library is used there (lazy module loading, the default), and that load
+ * does allocate device memory.  So make one call on each device at start-up,
+ * from a context that may allocate and outside any stream capture: that first
+ * call loads the kernels and the array, looks up the array's device address
+ * and raises the kernels' shared-memory limit, once per device.  From then on
+ * the array stays reserved on that device until the process exits, and calls
+ * allocate nothing.  All calls share the array and find the previous call's
+ * contents in it (each call rewrites what it reads): calls whose work overlaps
+ * on the GPU race on it, so serialise them. */
 GBFFT_API int fft_exec_noalloc(int64_t n, int64_t batch, int dir, const void* in, void* out, void* stream);
 
 /* Code of the last failing call on this host thread (FFT_OK if none). */

@@ -2,6 +2,12 @@
 
 Each translation unit is compiled in parallel; the shared library links the
 CUDA runtime statically so it loads without extra library paths.
+
+Beside it, the same objects with ``many.cu`` recompiled under
+``-DGBFFT_FAULT_INJECTION`` are linked into ``libgbfft_faultinject.so``, a
+test-only library in which an environment switch plants a missing producer in
+an uneven-batch plan (the bounded-wait timeout test).  The product library
+has no such switch.
 """
 from __future__ import annotations
 
@@ -16,6 +22,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbfft.so")
+FAULT_LIB = os.path.join(HERE, "libgbfft_faultinject.so")
+FAULT_SRC = "many.cu"          # the one source whose fault-injection build differs
+FAULT_FLAGS = ["-DGBFFT_FAULT_INJECTION"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
@@ -45,31 +54,39 @@ def _compile(src: str, obj: str, extra) -> str:
     return r.stderr
 
 
+def _link(out: str, objs) -> None:
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, out)
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
     dep_mtime = max(os.path.getmtime(p) for p in _deps())
+    fault_src = os.path.join(CSRC, FAULT_SRC)
+    fault_obj = os.path.join(BUILD, FAULT_SRC[:-3] + "_faultinject.o")
     jobs = []
-    for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+    for s, o, flags in [(s, os.path.join(BUILD, os.path.basename(s)[:-3] + ".o"), list(extra)) for s in srcs] + \
+            [(fault_src, fault_obj, list(extra) + FAULT_FLAGS)]:
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), dep_mtime):
-            jobs.append((s, o))
+            jobs.append((s, o, flags))
     if jobs:
         workers = min(len(jobs), max(1, os.cpu_count() or 1))
         with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-            futs = {ex.submit(_compile, s, o, list(extra)): s for s, o in jobs}
+            futs = {ex.submit(_compile, s, o, flags): s for s, o, flags in jobs}
             for f in cf.as_completed(futs):
                 msg = f.result()
                 if verbose and msg:
                     sys.stderr.write(msg)
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
     if force or jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        _link(LIB, objs)
+    if force or jobs or not os.path.exists(FAULT_LIB):
+        _link(FAULT_LIB, [fault_obj if os.path.basename(o) == FAULT_SRC[:-3] + ".o" else o for o in objs])
     return LIB
 
 

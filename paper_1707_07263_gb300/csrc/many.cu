@@ -242,6 +242,21 @@ __global__ void __launch_bounds__(kManyThreads, 4) many_kernel(const ManyArgs m)
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Fault injection for the bounded-wait test, compiled only into the test
+// library libgbfft_faultinject.so (nvcc -DGBFFT_FAULT_INJECTION); the product
+// library libgbfft.so has no such switch.  In the test library, a plan created
+// while GBFFT_FAULT_MISSING_PRODUCER=1 is set gets one row tile that waits for
+// a column tile that does not exist, with a ~1 ms wait budget, so the timeout
+// path is exercised without any GPU fault.
+#ifdef GBFFT_FAULT_INJECTION
+static bool fault_missing_producer() {
+  const char* e = getenv("GBFFT_FAULT_MISSING_PRODUCER");
+  return e && atoi(e) != 0;
+}
+#else
+static bool fault_missing_producer() { return false; }
+#endif
+
 int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
   if (count > (1 << 24)) return FFT_ERR_INVALID_ARG;
   std::vector<int> lg(count);
@@ -334,8 +349,9 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
   std::vector<ManyItem> items;
   items.insert(items.end(), fourstep.begin(), fourstep.end());
   items.insert(items.end(), batch_items.begin(), batch_items.end());
-  if (getenv("GBFFT_TEST_MISSING_PRODUCER") && atoi(getenv("GBFFT_TEST_MISSING_PRODUCER")) && !trs.empty()) {
-    // test hook: one row tile waits for a column tile that does not exist
+  const bool starve = fault_missing_producer();
+  if (starve && !trs.empty()) {
+    // injected fault: one row tile waits for a column tile that does not exist
     for (ManyItem& it : items)
       if (it.kind == 2) {
         it.need += 1;
@@ -420,8 +436,7 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
   m.done = d_cnt + 1;
   m.status = p->d_status;
   m.nitems = mp->nitems;
-  const bool starve = getenv("GBFFT_TEST_MISSING_PRODUCER") && atoi(getenv("GBFFT_TEST_MISSING_PRODUCER"));
-  m.wait_budget = starve ? 2000000LL : 4000000000LL;  // ~1 ms for the test hook, ~2 s otherwise
+  m.wait_budget = starve ? 2000000LL : 4000000000LL;  // ~1 ms under the injected fault, ~2 s otherwise
 
   p->n = total;
   p->ws_bytes = (size_t)ws_total * 8;

@@ -11,8 +11,11 @@
 // What it does: the same two-pass four-step FFT as fft_exec on a four-step
 // plan (column pass with twiddle, row pass written transposed), with its
 // scratch -- the pass-1 workspace and the twiddle tables -- carved out of one
-// file-scope static device array, g_noalloc_scratch, of fixed size.  Every GPU
-// that loads the library reserves that array until the process exits.
+// file-scope static device array, g_noalloc_scratch, of fixed size.  The CUDA
+// runtime loads this module (kernels and array) onto a device lazily, at the
+// library's first use there, and that load allocates; the array then stays
+// reserved on the device until the process exits.  The first call on a device
+// should therefore come at start-up, from a context that may allocate.
 //
 // The array is shared by every call on a device and keeps the previous call's
 // contents; nothing in it needs to start at zero (each call regenerates its
@@ -42,15 +45,48 @@ static __device__ __align__(256) float2 g_noalloc_scratch[kNoallocMaxPoints + kN
 
 // Host-side view: the symbol above is a host stand-in, not a device address.
 // The device address is looked up once per device (cudaGetSymbolAddress) and
-// cached here; kernels are set up for the larger shared-memory carve-out once
-// per device too.
+// cached here.  The same one-time set-up raises the dynamic shared-memory
+// limit of every tile kernel this entry point can launch, so later calls make
+// no attribute calls.
 constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static float2* g_noalloc_ptr[kMaxDevices];
 
+// Columns per tile of a pass of length 2^lg: 8192 points per tile, 1..16 columns.
+static int noalloc_cols(int lg) {
+  int c = (1 << 13) >> lg;
+  return c < 1 ? 1 : (c > 16 ? 16 : c);
+}
+
+// Split of n = 2^lgN into N1 = 2^lg1 (column pass) and N2 = 2^lg2 (row pass).
+static void noalloc_split(int lgN, int* lg1, int* lg2) {
+  *lg2 = (lgN + 1) / 2;
+  *lg1 = lgN - *lg2;
+}
+
+// The tile kernels of both passes.  Each pass is at least 2^7 long, so the
+// other pass always has more columns than one tile takes (noalloc_cols <= 16).
+static void noalloc_kernels(int lgN, const TileKernelInfo** k1, const TileKernelInfo** k2) {
+  int lg1, lg2;
+  noalloc_split(lgN, &lg1, &lg2);
+  *k1 = tile_kernel(MAP_CC, lg1, noalloc_cols(lg1));
+  *k2 = tile_kernel(MAP_JC, lg2, noalloc_cols(lg2));
+}
+
 static int noalloc_device_setup(int dev, float2** scratch) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
+    for (int lgN = kNoallocMinLog2; lgN <= kNoallocMaxLog2; ++lgN) {
+      const TileKernelInfo *k1, *k2;
+      noalloc_kernels(lgN, &k1, &k2);
+      if (!k1 || !k2) return FFT_ERR_UNSUPPORTED;
+      for (const TileKernelInfo* k : {k1, k2})
+        if (k->smem_bytes > 48 * 1024 &&
+            cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->smem_bytes) != cudaSuccess) {
+          cudaGetLastError();
+          return FFT_ERR_CUDA;
+        }
+    }
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -60,11 +96,6 @@ static int noalloc_device_setup(int dev, float2** scratch) {
   }
   *scratch = g_noalloc_ptr[dev];
   return FFT_OK;
-}
-
-static int noalloc_cols(int lg) {
-  int c = (1 << 13) >> lg;
-  return c < 1 ? 1 : (c > 16 ? 16 : c);
 }
 
 static int noalloc_launch(const TileKernelInfo* k, const TileArgs& a, long long ntiles, cudaStream_t s) {
@@ -78,23 +109,18 @@ static int noalloc_launch(const TileKernelInfo* k, const TileArgs& a, long long 
 static int noalloc_run(int64_t n, int64_t batch, int dir, const float2* in, float2* out, cudaStream_t s) {
   int lgN = 0;
   while ((1LL << lgN) < n) ++lgN;
-  const int lg2 = (lgN + 1) / 2, lg1 = lgN - lg2;
+  int lg1, lg2;
+  noalloc_split(lgN, &lg1, &lg2);
   const long long N1 = 1LL << lg1, N2 = 1LL << lg2;
-  const int c1 = (int)(noalloc_cols(lg1) < N2 ? noalloc_cols(lg1) : N2);
-  const int c2 = (int)(noalloc_cols(lg2) < N1 ? noalloc_cols(lg2) : N1);
-  const TileKernelInfo* k1 = tile_kernel(MAP_CC, lg1, c1);
-  const TileKernelInfo* k2 = tile_kernel(MAP_JC, lg2, c2);
-  if (!k1 || !k2) return FFT_ERR_UNSUPPORTED;
-  for (const TileKernelInfo* k : {k1, k2})
-    if (k->smem_bytes > 48 * 1024 &&
-        cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->smem_bytes) != cudaSuccess)
-      return FFT_ERR_CUDA;
+  const int c1 = noalloc_cols(lg1), c2 = noalloc_cols(lg2);
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FFT_ERR_CUDA;
   float2* scratch = nullptr;
   int rc = noalloc_device_setup(dev, &scratch);
   if (rc) return rc;
+  const TileKernelInfo *k1, *k2;
+  noalloc_kernels(lgN, &k1, &k2);
 
   // scratch layout: [workspace: n*batch points][tw1 4096][tw2 4096][lo 4096][hi 4096]
   float2* ws = scratch;
@@ -169,10 +195,9 @@ extern "C" GBFFT_API int fft_exec_noalloc(int64_t n, int64_t batch, int dir, con
       dir > 3 || !in || !out)
     return set_err(FFT_ERR_INVALID_ARG);
   if (((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return set_err(FFT_ERR_ALIGN);
-  int rc = noalloc_run(n, batch, dir, (const float2*)in, (float2*)out, (cudaStream_t)stream);
-  if (rc == FFT_OK && cudaPeekAtLastError() != cudaSuccess) {
-    cudaGetLastError();
-    rc = FFT_ERR_CUDA;
-  }
-  return set_err(rc);
+  // The twiddle launchers report through cudaGetLastError, which would also
+  // return an error left pending by an earlier, unrelated call on this thread:
+  // clear it first, so that every check below sees only this call's launches.
+  cudaGetLastError();
+  return set_err(noalloc_run(n, batch, dir, (const float2*)in, (float2*)out, (cudaStream_t)stream));
 }

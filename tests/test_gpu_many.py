@@ -117,15 +117,69 @@ def test_many_in_place_and_graph_replay(lib):
 
 def test_many_bounded_wait_reports_timeout(lib, monkeypatch):
     """A row tile told to wait for a column tile that never comes gives up
-    after its budget and reports FFT_ERR_TIMEOUT instead of hanging."""
-    monkeypatch.setenv("GBFFT_TEST_MISSING_PRODUCER", "1")
+    after its budget and reports FFT_ERR_TIMEOUT instead of hanging.  The
+    missing producer is planted by the test-only fault-injection build of the
+    library (the product library has no such switch)."""
+    from paper_1707_07263_gb300 import build_lib
+    flib = _lib.load(build_lib.FAULT_LIB)
+    monkeypatch.setenv("GBFFT_FAULT_MISSING_PRODUCER", "1")
     lengths = [1 << 14, 1 << 10, 1 << 16]
-    p = ManyPlan(lib, lengths, 0)
     x = torch.from_numpy(workloads.packed_cgauss(lengths, seed=3)).cuda()
+    p = ManyPlan(flib, lengths, 0)
     p.run(x, 0)
     torch.cuda.synchronize()
     assert p.status() == -5
-    monkeypatch.delenv("GBFFT_TEST_MISSING_PRODUCER")
-    p2 = ManyPlan(lib, lengths, 0)     # a fresh plan is unaffected
+    p_product = ManyPlan(lib, lengths, 0)   # the product library ignores the switch
+    p_product.run(x, 0)
+    assert p_product.status() == 0
+    monkeypatch.delenv("GBFFT_FAULT_MISSING_PRODUCER")
+    p2 = ManyPlan(flib, lengths, 0)     # a fresh plan is unaffected
     p2.run(x, 0)
     assert p2.status() == 0
+
+
+def test_many_config5_full_shape_forward_and_graph_gradient(lib):
+    """The uneven-batch workload at its stated shape: 4096 transforms with
+    lengths 2^e, e uniform over 8..16.  The forward result of every transform
+    is checked against the oracle; then the benchmark's graph-captured step
+    (forward, loss gradient 2 w^2 X, adjoint backward) is replayed and the
+    gradient of every transform is checked against the oracle gradient
+    2 F^H (w^2 F x) of L = sum |w X|^2."""
+    lengths = workloads.uneven_lengths(4096, seed=workloads.seed_for(4)).tolist()
+    total = int(sum(lengths))
+    xh = workloads.packed_cgauss(lengths, seed=workloads.seed_for(4, 2))
+    wh = workloads.real_weights(total, seed=workloads.seed_for(4, 1))
+    p = ManyPlan(lib, lengths, 0)
+    x = torch.from_numpy(xh).cuda()
+    X = p.run(x, 0)
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    check(X.cpu().numpy(), oracle_many(xh, lengths, 0), lengths, "cfg5 forward, 4096 transforms")
+
+    w2 = torch.from_numpy(2.0 * wh.astype(np.float32) ** 2).cuda()
+    G = torch.empty_like(x)
+    gx = torch.empty_like(x)
+    s = torch.cuda.Stream()
+
+    def step():
+        p.run(x, 0, X, stream=s)
+        torch.mul(X, w2, out=G)
+        p.run(G, 2, gx, stream=s)
+
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        step()
+    gx.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    got = gx.cpu().numpy()
+    o = 0
+    for n in lengths:
+        ref = oracle.spectral_loss_grad(xh[o:o + n].astype(np.complex128), wh[o:o + n].astype(np.float64))
+        err = oracle.rel_l2(got[o:o + n], ref)
+        assert err <= 1e-6 * np.log2(n), f"gradient, length {n} at {o}: {err:.3e}"
+        o += n

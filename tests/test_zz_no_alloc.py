@@ -1,10 +1,12 @@
-"""The allocation-free entry point fft_exec_noalloc against the planned path.
+"""The allocation-free entry point fft_exec_noalloc against the oracle and the
+planned path.
 
 fft_exec_noalloc serves callers that cannot allocate device memory when they
 need a transform (allocator callbacks, plug-ins in hosts that own all device
 memory, real-time paths).  It keeps its workspace and twiddles in a static
-device array shared by every call, so this test runs two different calls in a
-row and checks that each matches the result of the ordinary plan + fft_exec
+device array shared by every call, so this test runs several different calls
+in a row -- even and uneven splits of n, every direction, one in place -- and
+checks each against the FP64 oracle and against the ordinary plan + fft_exec
 path on the same input.  The file is named to be collected last.
 """
 from __future__ import annotations
@@ -34,8 +36,8 @@ def _planned(lib, x: torch.Tensor, n: int, batch: int, d: int) -> torch.Tensor:
     return out
 
 
-def _noalloc(lib, x: torch.Tensor, n: int, batch: int, d: int) -> torch.Tensor:
-    out = torch.empty_like(x)
+def _noalloc(lib, x: torch.Tensor, n: int, batch: int, d: int, in_place: bool = False) -> torch.Tensor:
+    out = x if in_place else torch.empty_like(x)
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = lib.fft_exec_noalloc(n, batch, d, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), s)
     assert rc == 0, _lib.ERRORS.get(rc, rc)
@@ -43,15 +45,34 @@ def _noalloc(lib, x: torch.Tensor, n: int, batch: int, d: int) -> torch.Tensor:
     return out
 
 
-def test_noalloc_matches_planned_path_twice_in_a_row():
+def _oracle(x: np.ndarray, d: int) -> np.ndarray:
+    """Every direction code: forward (Eq. 1), inverse (Eq. 2), adjoint of the
+    forward (conjugate direction, no 1/N), adjoint of the inverse (forward / N)."""
+    x = x.astype(np.complex128)
+    if d == 3:
+        return oracle.fft(x, oracle.FORWARD) / x.shape[-1]
+    return oracle.fft(x, d)
+
+
+# (n, batch, dir, seed, in place): calls in a row that differ in length, split
+# (2^15 and 2^21 split unevenly, 2^20 and 2^16 evenly), direction and placement
+CALLS = [(1 << 20, 2, 0, 11, False), (1 << 16, 5, 1, 12, False), (1 << 15, 128, 2, 13, False),
+         (1 << 21, 2, 3, 14, True), (1 << 20, 2, 0, 11, False)]
+
+
+def test_noalloc_matches_oracle_and_planned_path_calls_in_a_row():
     lib = _lib.load()
-    calls = [(1 << 20, 2, 0, 11), (1 << 16, 5, 1, 12)]   # (n, batch, dir, seed): two different calls
-    for n, batch, d, seed in calls:
-        x = torch.from_numpy(workloads.cgauss(n, batch, seed=seed).reshape(-1)).cuda()
-        ref = _planned(lib, x, n, batch, d).cpu().numpy().reshape(batch, n)
-        got = _noalloc(lib, x, n, batch, d).cpu().numpy().reshape(batch, n)
-        err = oracle.rel_l2_rows(got, ref).max()
-        assert err <= 5e-7 * np.log2(n), f"n={n} batch={batch} dir={d}: {err:.3e}"
+    for n, batch, d, seed, in_place in CALLS:
+        x = workloads.cgauss(n, batch, seed=seed)
+        xt = torch.from_numpy(x.reshape(-1)).cuda()
+        planned = _planned(lib, xt, n, batch, d).cpu().numpy().reshape(batch, n)
+        got = _noalloc(lib, xt, n, batch, d, in_place).cpu().numpy().reshape(batch, n)
+        tol = 5e-7 * np.log2(n)
+        what = f"n=2^{int(np.log2(n))} batch={batch} dir={d} in_place={in_place}"
+        err = oracle.rel_l2_rows(got, _oracle(x, d)).max()
+        assert err <= tol, f"{what}: vs oracle {err:.3e}"
+        err = oracle.rel_l2_rows(got, planned).max()
+        assert err <= tol, f"{what}: vs planned path {err:.3e}"
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
