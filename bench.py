@@ -19,7 +19,14 @@ Also printed on the same JSON line:
                 three streams), with the direct mode (kernels reading and
                 writing the host buffers) and the link's own ceiling
                 (concurrent copies up and down) beside it;
-  clocks        nvidia-smi samples taken during the timed region.
+  clocks        nvidia-smi samples taken during the timed region;
+  cfg1_latency, cfg3_large, cfg4_precision, cfg5_uneven
+                per-size results of the other configurations, measured on
+                the same GPU after the timed step (not part of it): time,
+                GFLOP/s, the algorithmic HBM fraction (16 B per point
+                whatever the pass count) beside the per-launch one, sampled
+                oracle errors, and whether the 70 % target at 2^20 and the
+                split-tensor-core-beats-FP32 target are met.
 
 ``--impl reference`` times the oracle instead (the deliberately slow CPU
 baseline) and prints the same line with "impl": "reference".
@@ -299,6 +306,160 @@ def cpu_model() -> str:
 
 
 # ------------------------------------------------------------------------------------
+# the other configurations, measured beside the headline (not part of its step)
+# ------------------------------------------------------------------------------------
+def measure_other_configs(torch, lib, dev, stream, peak, iters, warmup):
+    """Per-size results of the other configurations on the same GPU, outside
+    the headline's timed region: CUDA events on `stream`, `warmup` untimed and
+    `iters` timed executions, data resident in HBM, inputs larger than L2
+    where the configuration's size allows.  hbm_frac_algorithmic counts the
+    algorithmic 16 bytes per point (one complex64 read and one write) however
+    many passes the plan makes; hbm_frac_per_launch counts them once per
+    launch.  Errors are relative L2 against the FP64 oracle on sampled rows."""
+    import oracle
+    from paper_1707_07263_gb300 import _lib, api, tune, workloads
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    out = {}
+
+    def make(n, batch, prec=0, tuned=True, two_d=None):
+        if two_d:
+            h = lib.fft_plan_create_2d(two_d[0], two_d[1], 1, 0, 0)
+        elif tuned and prec == 0:
+            c = _lib.FftPlanConfig.from_dict(tune.tuned_config(n, batch, 0, dev))
+            h = lib.fft_plan_create_config(n, batch, 0, 0, ctypes.byref(c))
+        else:
+            h = lib.fft_plan_create(n, batch, 0, prec)
+        if not h:
+            return None, None
+        h = ctypes.c_void_p(h)
+        ws = lib.fft_plan_workspace_bytes(h)
+        wsb = torch.empty(ws, dtype=torch.uint8, device=dev) if ws else None
+        if ws:
+            _lib.check(lib.fft_plan_set_workspace(h, ctypes.c_void_p(wsb.data_ptr())))
+        return h, wsb
+
+    def timed(h, x, y, d=0, n_iter=iters):
+        def one():
+            _lib.check(lib.fft_exec_dir(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), d, sh))
+        return _time_fn(torch, one, n_iter, warmup, stream)
+
+    def entry(n_points, lg_sum, ms, launches):
+        gbs = 16.0 * n_points / (ms * 1e-3) / 1e9
+        return {"us": round(ms * 1e3, 2), "gflops": round(5.0 * n_points * lg_sum / (ms * 1e-3) / 1e9, 1),
+                "hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac_algorithmic": round(gbs / peak, 4),
+                "hbm_frac_per_launch": round(gbs * launches / peak, 4), "launches": launches}
+
+    # cfg1: one 4096-point transform (latency, not bandwidth)
+    n = 4096
+    x1 = torch.from_numpy(workloads.uniform(n, 1, workloads.seed_for(0)).reshape(-1)).to(dev)
+    y1 = torch.empty_like(x1)
+    h, _ = make(n, 1)
+    ms = timed(h, x1, y1, 0, max(200, iters))
+    ref = oracle.dft(x1.cpu().numpy().astype(np.complex128))
+    out["cfg1_latency"] = {"n": n, "batch": 1, "us_per_transform": round(ms * 1e3, 2),
+                           "gflops": round(flops(n, 1) / (ms * 1e-3) / 1e9, 2),
+                           "rel_l2": float(f"{oracle.rel_l2(y1.cpu().numpy(), ref):.3e}"),
+                           "note": "one CTA: launch-latency bound, roofline fraction not meaningful"}
+    lib.fft_destroy(h)
+
+    # cfg3: four-step 1-D (U[-1,1]) and the 8192 x 8192 SAR image
+    xu = torch.from_numpy(workloads.uniform(TOTAL, 1, workloads.seed_for(2)).reshape(-1)).to(dev)
+    y = torch.empty_like(xu)
+    res3 = {}
+    for lg, batch in ((20, 64), (24, 4), (26, 1)):
+        nn = 1 << lg
+        h, wsb = make(nn, batch)
+        ms = timed(h, xu, y)
+        res3[f"2^{lg}x{batch}"] = entry(TOTAL, lg, ms, lib.fft_plan_launches(h))
+        lib.fft_destroy(h)
+        del wsb
+    del xu
+    img = torch.from_numpy(workloads.sar_image(8192, 8192, seed=workloads.seed_for(2, 1)).reshape(-1)).to(dev)
+    h, wsb = make(0, 1, two_d=(8192, 8192))
+    ms = timed(h, img, y)
+    res3["8192x8192"] = entry(TOTAL, 26, ms, lib.fft_plan_launches(h))
+    lib.fft_destroy(h)
+    del wsb, img
+    f20 = res3["2^20x64"]["hbm_frac_algorithmic"]
+    out["cfg3_large"] = {"sizes": res3,
+                         "target_70pct_hbm_at_2p20": {"hbm_frac_algorithmic": f20, "met": bool(f20 >= 0.70)}}
+
+    # cfg4: FP32 against the tensor-core radix-16 variants, CN(0,1)
+    precs = [("fp32", 0), ("tc_bf16", 1), ("tc_fp16", 2), ("tc_bf16_split", 3), ("tc_fp16_split", 4)]
+    res4 = {}
+    for lg in (12, 16, 20):
+        nn = 1 << lg
+        batch = TOTAL // nn
+        xh = workloads.cgauss(nn, batch, seed=workloads.seed_for(3) + lg)
+        x = torch.from_numpy(xh.reshape(-1)).to(dev)
+        rows = 2
+        ref = oracle.fft(xh[:rows].astype(np.complex128))
+        del xh
+        for name, pc in precs:
+            h, wsb = make(nn, batch, pc)
+            if h is None:
+                res4[f"2^{lg}/{name}"] = {"unsupported": True}
+                continue
+            ms = timed(h, x, y)
+            e = entry(TOTAL, lg, ms, lib.fft_plan_launches(h))
+            got = y[: rows * nn].cpu().numpy().reshape(rows, nn)
+            e["rel_l2_max_sampled"] = float(f"{float(oracle.rel_l2_rows(got, ref).max()):.3e}")
+            res4[f"2^{lg}/{name}"] = e
+            lib.fft_destroy(h)
+            del wsb
+        del x
+    best = {}
+    for lg in (12, 16, 20):
+        t32 = res4[f"2^{lg}/fp32"]["us"]
+        split = [(res4[f"2^{lg}/{k}"]["us"], k) for k in ("tc_fp16_split", "tc_bf16_split")
+                 if "us" in res4.get(f"2^{lg}/{k}", {}) and res4[f"2^{lg}/{k}"]["rel_l2_max_sampled"] <= 1e-5]
+        best[f"2^{lg}"] = {"fp32_us": t32, "best_split_us": min(split)[0] if split else None,
+                           "split_faster_at_1e-5": bool(split and min(split)[0] < t32)}
+    out["cfg4_precision"] = {"variants": res4, "split_tc_vs_fp32": best}
+
+    # cfg5: 4096 uneven lengths, forward and the graph-captured gradient step
+    lengths = workloads.uneven_lengths(4096, seed=workloads.seed_for(4)).tolist()
+    total = int(sum(lengths))
+    xh = workloads.packed_cgauss(lengths, seed=workloads.seed_for(4, 2))
+    wh = workloads.real_weights(total, seed=workloads.seed_for(4, 1))
+    x = torch.from_numpy(xh).to(dev)
+    w2 = torch.from_numpy(2.0 * wh.astype(np.float32) ** 2).to(dev)
+    pm = api.Plan("many", (total,), len(lengths), 0, "fp32", dev, lengths=lengths)
+    X, G, gx = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+
+    def step():
+        pm.exec_ptr(x.data_ptr(), X.data_ptr(), 0, stream)
+        torch.mul(X, w2, out=G)
+        pm.exec_ptr(G.data_ptr(), gx.data_ptr(), 2, stream)
+
+    with torch.cuda.stream(stream):
+        step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        step()
+    ms_step = _time_fn(torch, g.replay, iters, warmup, stream)
+    ms_fwd = _time_fn(torch, lambda: pm.exec_ptr(x.data_ptr(), X.data_ptr(), 0, stream), iters, warmup, stream)
+    fl = sum(flops(nn, 1) for nn in lengths)
+    gxh = gx.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(lengths)])
+    errs = [oracle.rel_l2(gxh[offs[i]:offs[i + 1]],
+                          oracle.spectral_loss_grad(xh[offs[i]:offs[i + 1]].astype(np.complex128),
+                                                    wh[offs[i]:offs[i + 1]].astype(np.float64)))
+            for i in range(0, len(lengths), 97)]
+    gbs = 16.0 * total / (ms_fwd * 1e-3) / 1e9
+    out["cfg5_uneven"] = {"transforms": len(lengths), "points": total, "forward_us": round(ms_fwd * 1e3, 1),
+                          "gflops_fwd": round(fl / (ms_fwd * 1e-3) / 1e9, 1),
+                          "hbm_frac_algorithmic_fwd": round(gbs / peak, 4),
+                          "graph_step_us": round(ms_step * 1e3, 1),
+                          "gflops_fwd_plus_bwd": round(2 * fl / (ms_step * 1e-3) / 1e9, 1),
+                          "grad_rel_l2_max_sampled": float(f"{max(errs):.3e}"), "grad_samples": len(errs),
+                          "step": "graph-captured: forward (one launch), 2 w^2 X (torch), adjoint (one launch)"}
+    pm.close()
+    return out
+
+
+# ------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------
 def run_gpu(args):
@@ -412,6 +573,11 @@ def run_gpu(args):
         per_size[lab] = {"us": round(per_item_ms[i] * 1e3, 2),
                          "gflops": round(flops(nn, bb) / (per_item_ms[i] * 1e-3) / 1e9, 1),
                          "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
+
+    # ---- the other configurations (per size, outside the timed step) ----
+    others = {}
+    if rank == 0 and not args.no_extra:
+        others = measure_other_configs(torch, lib, dev, stream, peak, max(10, K // 2), args.warmup)
 
     # ---- end to end through the public API with pinned host buffers ----
     e2e = None
@@ -543,6 +709,7 @@ def run_gpu(args):
         "plans": {f"2^{int(np.log2(n))}": _describe(lib, plans[(n, b)][0]) for _, n, b, _ in items},
         "autotuned": tuned if args.tuned else None,
     }
+    line.update(others)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -952,6 +1119,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the per-size results of configurations 1, 3, 4, 5")
     ap.add_argument("--case", type=int, default=0, help="run one plan of 2^CASE points (profiling case)")
     ap.add_argument("--tuned", type=int, default=1, help="1: plans from the autotuner (default), 0: planner defaults")
     ap.add_argument("--batch", type=int, default=0)

@@ -118,8 +118,18 @@ GBFFT_API fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, in
  * transform of length n/2 and one split step give the result.  n <= 2^15: one
  * fused kernel, one read and one write of every value.  Longer n: the complex
  * plan plus one split kernel, with a workspace (fft_plan_workspace_bytes).
+ * The adjoints (for backpropagation; adjoint with respect to the real inner
+ * product <u, v> = Re sum conj(u) v, which is PyTorch's gradient convention):
+ *   FFT_ADJOINT (adjoint of FFT_FORWARD): in = rows of n/2 + 1 complex64 g,
+ *     out = rows of n floats  y[m] = Re sum_{k=0}^{n/2} g[k] W_n^{-mk}
+ *     (Eq. 4 over the kept bins; Im g[0] and Im g[n/2] do not enter).
+ *   FFT_INVERSE | FFT_ADJOINT (adjoint of FFT_INVERSE): in = rows of n floats
+ *     g, out = rows of n/2 + 1 complex64: Eq. 1 of g with bins 1..n/2-1 times
+ *     2/n and bins 0 and n/2 times 1/n.
+ * Both run in the same kernels as the transforms (the bin weights and the
+ * scale are arguments of the split step), at the same cost.
  * Pointers 8-byte aligned, device memory or memory fft_pointer_usable accepts;
- * in == out is not allowed.  Other directions return FFT_ERR_INVALID_ARG. */
+ * in == out is not allowed. */
 GBFFT_API fft_plan* fft_plan_create_r2c(int64_t n, int64_t batch, int prec);
 
 /* Plan for `count` 1-D transforms of uneven power-of-two lengths lengths[i]
@@ -160,6 +170,16 @@ GBFFT_API int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, v
  * capturable.  FFT_ERR_UNSUPPORTED for 2-D, uneven-batch, tensor-core and
  * fused two-pass plans. */
 GBFFT_API int fft_exec_filter(fft_plan* plan, const void* in, void* out, const void* filt, void* stream);
+
+/* As fft_exec_filter, with a direction: FFT_FORWARD is fft_exec_filter, and
+ * FFT_ADJOINT computes the adjoint of range compression,
+ *     y_b = IFFT( conj(H) .* FFT(x_b) )
+ * (the adjoint of F^-1 diag(H) F is F^-1 diag(conj H) F, since F^-1 = F^H / n),
+ * which is the backward pass of range compression with respect to x: the same
+ * kernels, with the filter conjugated as it is loaded.  Other directions
+ * return FFT_ERR_INVALID_ARG. */
+GBFFT_API int fft_exec_filter_dir(fft_plan* plan, const void* in, void* out, const void* filt, int dir,
+                                  void* stream);
 
 /* Whether the GPU can read and write the `bytes` bytes at `ptr` through that
  * same address, so that fft_exec may take it as `in` or `out`: memory of the

@@ -69,6 +69,7 @@ SIGNATURES = {
                             ctypes.POINTER(ctypes.c_float)]),
     "fft_pointer_usable": (_int, [_vp, _sz]),
     "fft_exec_filter": (_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fft_exec_filter_dir": (_int, [_vp, _vp, _vp, _vp, _int, _vp]),
     "fft_last_error": (_int, []),
     "fft_error_string": (ctypes.c_char_p, [_int]),
 }

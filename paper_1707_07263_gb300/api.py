@@ -126,11 +126,12 @@ class Plan:
         self.exec_ptr(x.data_ptr(), out.data_ptr(), dir, stream)
         return out
 
-    def exec_filter_ptr(self, in_ptr: int, out_ptr: int, filt_ptr: int, stream=None) -> None:
-        """Range compression IFFT(H * FFT(row)) of every row (fft_exec_filter)."""
-        rc = self.lib.fft_exec_filter(self.handle, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
-                                      ctypes.c_void_p(filt_ptr), ctypes.c_void_p(_stream_handle(stream)))
-        L.check(rc, "fft_exec_filter")
+    def exec_filter_ptr(self, in_ptr: int, out_ptr: int, filt_ptr: int, stream=None, dir: int = FORWARD) -> None:
+        """Range compression IFFT(H * FFT(row)) of every row, or with
+        dir=ADJOINT its adjoint IFFT(conj(H) * FFT(row)) (fft_exec_filter_dir)."""
+        rc = self.lib.fft_exec_filter_dir(self.handle, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+                                          ctypes.c_void_p(filt_ptr), int(dir), ctypes.c_void_p(_stream_handle(stream)))
+        L.check(rc, "fft_exec_filter_dir")
 
     def status(self, stream=None) -> int:
         return int(self.lib.fft_status(self.handle, ctypes.c_void_p(_stream_handle(stream))))
@@ -282,21 +283,21 @@ def fft_many(packed: torch.Tensor, lengths, inverse: bool = False, prec="fp32") 
     return _FFTMany.apply(packed.reshape(-1), lengths, INVERSE if inverse else FORWARD, prec)
 
 
-def _run_filter(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
+def _run_filter(x: torch.Tensor, H: torch.Tensor, dir: int = FORWARD) -> torch.Tensor:
     n = x.shape[-1]
     batch = x.numel() // n if n else 0
     out = torch.empty_like(x)
     if batch == 0:
         return out
     p = get_plan("1d", (n,), batch, "fp32", x.device)
-    p.exec_filter_ptr(x.data_ptr(), out.data_ptr(), H.data_ptr())
+    p.exec_filter_ptr(x.data_ptr(), out.data_ptr(), H.data_ptr(), dir=dir)
     return out
 
 
 class _RangeCompress(torch.autograd.Function):
-    """y = F^{-1} diag(H) F x per row.  Its adjoint is F^{-1} diag(conj H) F,
-    so the backward pass is the same fused operation with the conjugated
-    filter (no gradient for H)."""
+    """y = F^{-1} diag(H) F x per row.  Its adjoint is F^{-1} diag(conj H) F:
+    the backward pass is one library call, the same fused kernels with the
+    filter conjugated as it is loaded (no gradient for H)."""
 
     @staticmethod
     def forward(ctx, x, H):
@@ -306,7 +307,7 @@ class _RangeCompress(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         (H,) = ctx.saved_tensors
-        return _run_filter(g.contiguous(), H.conj().resolve_conj().contiguous()), None
+        return _run_filter(g.contiguous(), H, ADJOINT), None
 
 
 def range_compress(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
@@ -324,13 +325,15 @@ def range_compress(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
 
 
 def _run_real(x: torch.Tensor, n: int, dir: int) -> torch.Tensor:
-    """Real-to-complex (dir FORWARD: float32 rows of n -> complex64 rows of
-    n/2 + 1) or complex-to-real (dir INVERSE) through a cached real plan."""
+    """Through a cached real plan: real-to-complex (dir FORWARD, float32 rows
+    of n -> complex64 rows of n/2 + 1) or complex-to-real (dir INVERSE), and
+    their adjoints (ADJOINT: complex rows -> real rows; INVERSE | ADJOINT:
+    real rows -> complex rows)."""
     rows = x.shape[:-1]
     batch = 1
     for d in rows:
         batch *= int(d)
-    if dir == FORWARD:
+    if dir in (FORWARD, INVERSE | ADJOINT):
         out = torch.empty(rows + (n // 2 + 1,), dtype=torch.complex64, device=x.device)
     else:
         out = torch.empty(rows + (n,), dtype=torch.float32, device=x.device)
@@ -343,8 +346,8 @@ def _run_real(x: torch.Tensor, n: int, dir: int) -> torch.Tensor:
 
 class _RFFT(torch.autograd.Function):
     """X = rfft(x).  For real x the gradient is Re(sum_k g_k W^{-nk}) over the
-    kept outputs, i.e. n * irfft(G) with G = g except the interior bins
-    halved (irfft counts each of them twice)."""
+    kept outputs: the adjoint of the real-to-complex transform, one library
+    call (FFT_ADJOINT on the real plan)."""
 
     @staticmethod
     def forward(ctx, x):
@@ -353,15 +356,14 @@ class _RFFT(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g):
-        n = ctx.n
-        G = g.contiguous().clone()
-        G[..., 1:n // 2] *= 0.5
-        return _run_real(G, n, INVERSE) * n
+        return _run_real(g.contiguous(), ctx.n, ADJOINT)
 
 
 class _IRFFT(torch.autograd.Function):
-    """x = irfft(X, n).  The gradient is rfft(g) / n with the interior bins
-    doubled (each stands for itself and its conjugate partner)."""
+    """x = irfft(X, n).  The gradient is the adjoint of the complex-to-real
+    transform: Eq. 1 of g with the interior bins times 2/n (each stands for
+    itself and its conjugate partner) and bins 0, n/2 times 1/n, one library
+    call (FFT_INVERSE | FFT_ADJOINT on the real plan)."""
 
     @staticmethod
     def forward(ctx, X, n):
@@ -370,10 +372,7 @@ class _IRFFT(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g):
-        n = ctx.n
-        R = _run_real(g.contiguous(), n, FORWARD)
-        R[..., 1:n // 2] *= 2.0
-        return R / n, None
+        return _run_real(g.contiguous(), ctx.n, INVERSE | ADJOINT), None
 
 
 def rfft(x: torch.Tensor) -> torch.Tensor:

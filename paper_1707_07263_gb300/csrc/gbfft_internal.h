@@ -61,9 +61,9 @@ cudaError_t launch_gen_twiddles_n64(double2* tab, long long N, long long count, 
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false);
 cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);
 cudaError_t launch_r2c_split(const float2* z, float2* x, long long M, long long batch, const float2* lo,
-                             const float2* hi, int s, cudaStream_t st);
+                             const float2* hi, int s, float s_int, float s_end, cudaStream_t st);
 cudaError_t launch_c2r_split(const float2* x, float2* z, long long M, long long batch, const float2* lo,
-                             const float2* hi, int s, cudaStream_t st);
+                             const float2* hi, int s, float end_mul, cudaStream_t st);
 
 }  // namespace gbfft
 

@@ -339,7 +339,8 @@ static int exec_passes(fft_plan* p, const float2* in, float2* out, int dir, cuda
 // transform whose last (row) pass stores conj(H X); the second is a forward
 // transform of that, conjugated and scaled by 1/N on its last store, which is
 // Eq. 2 applied to H X.  `out` holds the intermediate.
-static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const float2* filt, cudaStream_t s) {
+static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const float2* filt, int conj_filt,
+                            cudaStream_t s) {
   if (p->prec != FFT_PREC_FP32) return FFT_ERR_UNSUPPORTED;
   const float inv_n = (float)(1.0 / (double)p->n);
   if (p->kind == KIND_SINGLE) {
@@ -359,6 +360,7 @@ static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const fl
     a.tw_rev = p->d_rctw ? (const float2*)p->d_rctw : p->tw1;
     a.filt = filt;
     a.filt_mask = L - 1;
+    a.filt_conj = conj_filt;
     a.scale_out = 1;
     a.sx = inv_n;
     a.sy = -inv_n;
@@ -388,6 +390,7 @@ static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const fl
         if (run == 0) {
           a.filt = filt;
           a.filt_mask = p->n - 1;
+          a.filt_conj = conj_filt;
           a.sx = 1.0f;
           a.sy = -1.0f;
         } else {
@@ -408,11 +411,21 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s);
 
 // ---- real-data transforms (KIND_REAL): N = 2M reals per row ----------------
 static int exec_real(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
-  if (dir != FFT_FORWARD && dir != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
+  if (dir < 0 || dir > (FFT_INVERSE | FFT_ADJOINT)) return FFT_ERR_INVALID_ARG;
   if ((const void*)in == (const void*)out) return FFT_ERR_INVALID_ARG;
   const long long M = p->n / 2;
+  // Real rows in, complex rows out: the transform (FFT_FORWARD) and the adjoint
+  // of the complex-to-real transform (FFT_INVERSE | FFT_ADJOINT), which is the
+  // same split with the interior outputs times 2/N and X[0], X[M] times 1/N.
+  // Complex rows in, real rows out: the inverse (FFT_INVERSE, 1/N) and the
+  // adjoint of the real-to-complex transform (FFT_ADJOINT), which doubles the
+  // real parts of X[0] and X[M] and drops the 1/N.
+  const bool to_complex = dir == FFT_FORWARD || dir == (FFT_INVERSE | FFT_ADJOINT);
+  const bool adj = (dir & FFT_ADJOINT) != 0;
+  const float s_int = adj ? (float)(1.0 / (double)M) : 1.0f;   // 2/N
+  const float s_end = adj ? (float)(0.5 / (double)M) : 1.0f;   // 1/N
   if (p->kr2c) {
-    const TileKernelInfo* k = dir == FFT_FORWARD ? p->kr2c : p->kc2r;
+    const TileKernelInfo* k = to_complex ? p->kr2c : p->kc2r;
     const int C = k->C;
     TileArgs a;
     base_args(a);
@@ -423,12 +436,17 @@ static int exec_real(fft_plan* p, const float2* in, float2* out, int dir, cudaSt
     a.ncols = p->batch;
     a.r_w = p->r_lo;   // one-level table W_N^k, k < M
     a.in_sn = a.out_sn = 1;
-    if (dir == FFT_FORWARD) {
+    if (to_complex) {
       // rows of M complex (2M reals) in, rows of M + 1 complex out
       a.in_gstride = (long long)C * M;
       a.in_sc = M;
       a.out_gstride = (long long)C * (M + 1);
       a.out_sc = M + 1;
+      if (adj) {
+        a.scale_out = 1;
+        a.sx = s_int;
+        a.sy = s_end;
+      }
     } else {
       a.in_gstride = (long long)C * (M + 1);
       a.in_sc = M + 1;
@@ -436,20 +454,23 @@ static int exec_real(fft_plan* p, const float2* in, float2* out, int dir, cudaSt
       a.out_sc = M;
       a.conj_in = 1;
       a.scale_out = 1;
-      a.sx = (float)(1.0 / (double)M);
+      a.sx = adj ? 1.0f : (float)(1.0 / (double)M);
       a.sy = -a.sx;
+      a.r_end2 = adj ? 1 : 0;
     }
     return launch_tile(k, a, a.tiles_per_batch, s);
   }
   if (!p->inner || !p->zbuf) return FFT_ERR_NO_WORKSPACE;
-  if (dir == FFT_FORWARD) {
+  if (to_complex) {
     const int rc = exec_plan(p->inner, in, p->zbuf, FFT_FORWARD, s);
     if (rc) return rc;
-    return launch_r2c_split(p->zbuf, out, M, p->batch, p->r_lo, p->r_hi, p->r_s, s) == cudaSuccess ? FFT_OK
-                                                                                                  : FFT_ERR_CUDA;
+    return launch_r2c_split(p->zbuf, out, M, p->batch, p->r_lo, p->r_hi, p->r_s, s_int, s_end, s) == cudaSuccess
+               ? FFT_OK
+               : FFT_ERR_CUDA;
   }
-  if (launch_c2r_split(in, p->zbuf, M, p->batch, p->r_lo, p->r_hi, p->r_s, s) != cudaSuccess) return FFT_ERR_CUDA;
-  return exec_plan(p->inner, p->zbuf, out, FFT_INVERSE, s);
+  if (launch_c2r_split(in, p->zbuf, M, p->batch, p->r_lo, p->r_hi, p->r_s, adj ? 2.0f : 1.0f, s) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  return exec_plan(p->inner, p->zbuf, out, adj ? FFT_ADJOINT : FFT_INVERSE, s);
 }
 
 int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
@@ -1221,15 +1242,19 @@ int fft_exec_dir(fft_plan* plan, const void* in, void* out, int dir, void* strea
   return set_err(exec_plan(plan, in, out, dir, (cudaStream_t)stream));
 }
 
-int fft_exec_filter(fft_plan* plan, const void* in, void* out, const void* filt, void* stream) {
-  if (!is_live(plan) || !in || !out || !filt) return set_err(FFT_ERR_INVALID_ARG);
+int fft_exec_filter_dir(fft_plan* plan, const void* in, void* out, const void* filt, int dir, void* stream) {
+  if (!is_live(plan) || !in || !out || !filt || (dir != FFT_FORWARD && dir != FFT_ADJOINT))
+    return set_err(FFT_ERR_INVALID_ARG);
   if (((uintptr_t)in & 7) || ((uintptr_t)out & 7) || ((uintptr_t)filt & 7)) return set_err(FFT_ERR_ALIGN);
-  int rc = exec_filter_plan(plan, (const float2*)in, (float2*)out, (const float2*)filt, (cudaStream_t)stream);
-  if (rc == FFT_OK && cudaPeekAtLastError() != cudaSuccess) {
-    cudaGetLastError();
-    rc = FFT_ERR_CUDA;
-  }
-  return set_err(rc);
+  // every launch below reports its own error; one left pending by an earlier,
+  // unrelated call must not be taken for this call's
+  cudaGetLastError();
+  return set_err(exec_filter_plan(plan, (const float2*)in, (float2*)out, (const float2*)filt,
+                                  dir == FFT_ADJOINT ? 1 : 0, (cudaStream_t)stream));
+}
+
+int fft_exec_filter(fft_plan* plan, const void* in, void* out, const void* filt, void* stream) {
+  return fft_exec_filter_dir(plan, in, out, filt, FFT_FORWARD, stream);
 }
 
 void fft_destroy(fft_plan* plan) {

@@ -15,8 +15,10 @@ __device__ __forceinline__ float2 w_two_level(const float2* lo, const float2* hi
 
 // X[k] = E + W_N^k O, E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / (2i),
 // for the pair k = q, M - q (q = 0..M/2; Z[M] = Z[0], W_N^M = -1).
+// Outputs X[1..M-1] are multiplied by s_int, X[0] and X[M] by s_end (1 and 1
+// for the transform; 2/N and 1/N for the adjoint of the complex-to-real one).
 __global__ void r2c_split_kernel(const float2* __restrict__ z, float2* __restrict__ x, long long M, long long batch,
-                                 const float2* lo, const float2* hi, int s) {
+                                 const float2* lo, const float2* hi, int s, float s_int, float s_end) {
   const long long half = M / 2 + 1;
   const long long total = half * batch;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -30,21 +32,27 @@ __global__ void r2c_split_kernel(const float2* __restrict__ z, float2* __restric
     {
       const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
       const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-      __stcs(xr + q, cadd(e, cmul(w, o)));
+      const float sc = q == 0 ? s_end : s_int;
+      const float2 xq = cadd(e, cmul(w, o));
+      __stcs(xr + q, make_float2(xq.x * sc, xq.y * sc));
     }
     if (M - q != q) {
       // the partner output M - q: roles of zk and zm swap, W_N^{M-q} = -conj(W_N^q)
       const float2 e = make_float2(0.5f * (zm.x + zk.x), 0.5f * (zm.y - zk.y));
       const float2 o = make_float2(0.5f * (zm.y + zk.y), -0.5f * (zm.x - zk.x));
-      __stcs(xr + (M - q), cadd(e, cmul(make_float2(-w.x, w.y), o)));
+      const float sc = q == 0 ? s_end : s_int;   // q == 0: the partner is X[M]
+      const float2 xm = cadd(e, cmul(make_float2(-w.x, w.y), o));
+      __stcs(xr + (M - q), make_float2(xm.x * sc, xm.y * sc));
     }
   }
 }
 
 // Z[k] = E + i O, E = (X[k] + conj X[M-k]) / 2, O = (X[k] - conj X[M-k]) W_N^{-k} / 2,
 // for the pair k = q, M - q (q = 0..M/2; M - q < M only); Im X[0], Im X[M] do not enter.
+// end_mul multiplies the real parts of X[0] and X[M] (1 for the transform, 2
+// for the adjoint of the real-to-complex transform).
 __global__ void c2r_split_kernel(const float2* __restrict__ x, float2* __restrict__ z, long long M, long long batch,
-                                 const float2* lo, const float2* hi, int s) {
+                                 const float2* lo, const float2* hi, int s, float end_mul) {
   const long long half = M / 2 + 1;
   const long long total = half * batch;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -55,8 +63,8 @@ __global__ void c2r_split_kernel(const float2* __restrict__ x, float2* __restric
     float2 xk = __ldcs(xr + q);
     float2 xm = __ldcs(xr + (M - q));
     if (q == 0) {
-      xk.y = 0.f;
-      xm.y = 0.f;
+      xk = make_float2(xk.x * end_mul, 0.f);
+      xm = make_float2(xm.x * end_mul, 0.f);
     }
     const float2 w = w_two_level(lo, hi, s, q);
     {
@@ -81,14 +89,14 @@ static unsigned split_grid(long long total) {
 }
 
 cudaError_t launch_r2c_split(const float2* z, float2* x, long long M, long long batch, const float2* lo,
-                             const float2* hi, int s, cudaStream_t st) {
-  r2c_split_kernel<<<split_grid((M / 2 + 1) * batch), 256, 0, st>>>(z, x, M, batch, lo, hi, s);
+                             const float2* hi, int s, float s_int, float s_end, cudaStream_t st) {
+  r2c_split_kernel<<<split_grid((M / 2 + 1) * batch), 256, 0, st>>>(z, x, M, batch, lo, hi, s, s_int, s_end);
   return cudaGetLastError();
 }
 
 cudaError_t launch_c2r_split(const float2* x, float2* z, long long M, long long batch, const float2* lo,
-                             const float2* hi, int s, cudaStream_t st) {
-  c2r_split_kernel<<<split_grid((M / 2 + 1) * batch), 256, 0, st>>>(x, z, M, batch, lo, hi, s);
+                             const float2* hi, int s, float end_mul, cudaStream_t st) {
+  c2r_split_kernel<<<split_grid((M / 2 + 1) * batch), 256, 0, st>>>(x, z, M, batch, lo, hi, s, end_mul);
   return cudaGetLastError();
 }
 

@@ -175,12 +175,26 @@ struct TileArgs {
   // filt[o & filt_mask] (filt_mask = N - 1, rows N apart) before the scaling.
   const float2* filt;
   long long filt_mask;
+  int filt_conj;    // 1: multiply by conj(filt[k]) instead (the adjoint of range compression)
   // Stage table of the remainder-last schedule (REV passes).
   const float2* tw_rev;
   // Real-data transforms of length N = 2L (rows of L complex values = 2L
   // reals): r_w[k] = W_N^k, k < L.
   const float2* r_w;
+  // Complex-to-real first pass (PRE == 5): 1 doubles the real parts of X[0]
+  // and X[L] (with the scale 1 instead of 1/L this is the adjoint of the
+  // real-to-complex transform).  The real-to-complex last pass (POST == 3)
+  // takes scale_out: outputs X[1..L-1] times sx, X[0] and X[L] times sy (the
+  // adjoint of the complex-to-real transform has sx = 2/N, sy = 1/N).
+  int r_end2;
 };
+
+// Filter value of range compression at frequency index k (conjugated for the
+// adjoint).
+__device__ __forceinline__ float2 filt_at(const TileArgs& a, long long k) {
+  const float2 f = __ldg(a.filt + k);
+  return a.filt_conj ? make_float2(f.x, -f.y) : f;
+}
 
 template <int R>
 __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, int NS, int k) {
@@ -275,6 +289,10 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
         if (jj[i] == 0) {   // n == 0 only for r == 0
           x1[0].y = 0.f;
           x2[0].y = 0.f;
+          if (a.r_end2) {
+            x1[0].x *= 2.f;
+            x2[0].x *= 2.f;
+          }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -366,7 +384,11 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
         const float2 zm = zr[pidx((L - k) & (L - 1))];
         const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        const float2 x = cadd(e, cmul(__ldg(a.r_w + k), o));
+        float2 x = cadd(e, cmul(__ldg(a.r_w + k), o));
+        if (a.scale_out) {
+          const float sc = k == 0 ? a.sy : a.sx;
+          x = make_float2(x.x * sc, x.y * sc);
+        }
         if (a.stream_out)
           __stcs(orow + k, x);
         else
@@ -375,7 +397,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       if (j == 0) {
         // X[L] = E[0] - O[0] (W_N^L = -1)
         const float2 z0 = v[0];
-        const float2 x = make_float2(z0.x - z0.y, 0.f);
+        const float2 x = make_float2((z0.x - z0.y) * (a.scale_out ? a.sy : 1.f), 0.f);
         if (a.stream_out)
           __stcs(orow + L, x);
         else
@@ -388,7 +410,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
     const int j = jj[0];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      const float2 z = cmul(v[q], __ldg(a.filt + j + q * NS));
+      const float2 z = cmul(v[q], filt_at(a, j + q * NS));
       v[q] = make_float2(z.x, -z.y);
     }
   } else if constexpr (LAST && REV) {
@@ -436,7 +458,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
         const long long o = (long long)(gout - a.out) + c * a.out_sc + (long long)j * a.out_sn;
         const long long st = (long long)NS * a.out_sn;
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = cmul(v[q], __ldg(a.filt + ((o + q * st) & a.filt_mask)));
+        for (int q = 0; q < R; ++q) v[q] = cmul(v[q], filt_at(a, (o + q * st) & a.filt_mask));
       }
     }
     if (a.scale_out) {

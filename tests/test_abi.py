@@ -101,6 +101,8 @@ def test_null_plan_calls(lib):
     assert lib.fft_exec(None, None, None, None) == -1
     assert lib.fft_exec_dir(None, None, None, 0, None) == -1
     assert lib.fft_exec_filter(None, None, None, None, None) == -1
+    assert lib.fft_exec_filter_dir(None, None, None, None, 0, None) == -1
+    assert lib.fft_exec_filter_dir(None, None, None, None, 2, None) == -1
     assert lib.fft_pointer_usable(None, 8) == -1
     assert lib.fft_plan_workspace_bytes(None) == 0
     assert lib.fft_plan_set_workspace(None, None) == -1
@@ -195,6 +197,7 @@ def test_pointers_that_are_not_live_plans(lib):
     assert lib.fft_exec(fake, p, p, None) == -1
     assert lib.fft_exec_dir(fake, p, p, 0, None) == -1
     assert lib.fft_exec_filter(fake, p, p, p, None) == -1
+    assert lib.fft_exec_filter_dir(fake, p, p, p, 2, None) == -1
     assert lib.fft_plan_set_workspace(fake, None) == -1
     assert lib.fft_status(fake, None) == -1
     assert lib.fft_plan_workspace_bytes(fake) == 0 and lib.fft_plan_launches(fake) == 0

@@ -36,6 +36,7 @@ int main(void) {
     CHECK(fft_exec(NULL, NULL, NULL, NULL) == FFT_ERR_INVALID_ARG);
     CHECK(fft_exec_dir(NULL, NULL, NULL, FFT_INVERSE | FFT_ADJOINT, NULL) == FFT_ERR_INVALID_ARG);
     CHECK(fft_exec_filter(NULL, NULL, NULL, NULL, NULL) == FFT_ERR_INVALID_ARG);
+    CHECK(fft_exec_filter_dir(NULL, NULL, NULL, NULL, FFT_ADJOINT, NULL) == FFT_ERR_INVALID_ARG);
     CHECK(fft_plan_workspace_bytes(NULL) == 0);
     CHECK(fft_plan_launches(NULL) == 0);
     CHECK(strcmp(fft_error_string(FFT_OK), "ok") == 0);

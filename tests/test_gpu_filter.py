@@ -155,6 +155,22 @@ def test_range_compress_autograd():
     assert oracle.rel_l2(xt.grad.cpu().numpy(), g_ref) <= 2 * tol(n)
 
 
+@pytest.mark.parametrize("lg,batch", [(1, 3), (6, 70), (10, 9), (12, 5), (14, 3), (16, 2), (20, 1)])
+def test_adjoint_direction(lg, batch):
+    """fft_exec_filter_dir(FFT_ADJOINT) is range compression with conj(H):
+    one-pass lengths through the fused kernel, longer ones through the passes
+    run twice."""
+    n = 1 << lg
+    x = workloads.cgauss(n, batch, seed=5300 + lg)
+    H = workloads.cgauss(n, 1, seed=5400 + lg)[0]
+    xd, Hd = torch.from_numpy(x).cuda(), torch.from_numpy(H).cuda()
+    p = gb.get_plan("1d", (n,), batch)
+    out = torch.empty_like(xd)
+    p.exec_filter_ptr(xd.data_ptr(), out.data_ptr(), Hd.data_ptr(), dir=L.FFT_ADJOINT)
+    torch.cuda.synchronize()
+    assert_rc(out.cpu().numpy(), x, np.conj(H), f"adjoint N=2^{lg}")
+
+
 def test_range_compress_shapes_and_empty():
     n = 256
     x = workloads.cgauss(n, 6, seed=5200).reshape(2, 3, n)
@@ -178,6 +194,9 @@ def test_filter_errors():
     assert lib.fft_exec_filter(None, dp, dp, ctypes.c_void_p(H.data_ptr()), nul) == -1
     odd = ctypes.c_void_p(H.data_ptr() + 4)
     assert lib.fft_exec_filter(p.handle, dp, dp, odd, nul) == -2
+    Hp = ctypes.c_void_p(H.data_ptr())
+    for bad in (L.FFT_INVERSE, L.FFT_INVERSE | L.FFT_ADJOINT, 7, -1):
+        assert lib.fft_exec_filter_dir(p.handle, dp, dp, Hp, bad, nul) == -1
     p2 = gb.get_plan("2d", (64, 64), 1)
     assert lib.fft_exec_filter(p2.handle, dp, dp, ctypes.c_void_p(H.data_ptr()), nul) == -6
     ptc = gb.get_plan("1d", (4096,), 2, prec="tc_bf16")

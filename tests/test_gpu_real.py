@@ -138,6 +138,45 @@ def test_irfft_gradient_finite_differences():
     assert oracle.rel_l2(Xt.grad.cpu().numpy(), fd) <= 1e-5
 
 
+@pytest.mark.parametrize("lg", [2, 3, 5, 8, 11, 12, 15, 16, 18])
+def test_real_adjoints_match_oracle(lg):
+    """The adjoints of the real transforms (FFT_ADJOINT and FFT_INVERSE |
+    FFT_ADJOINT on a real plan) against their definitions written with the
+    oracle:  R2C^T g = Re(sum_{k<=n/2} g_k W^{-mk})  (Eq. 4 over the kept bins,
+    i.e. the oracle's adjoint transform of g zero-padded to n, real part), and
+    C2R^T g = Eq. 1 of g with bins 1..n/2-1 times 2/n and bins 0, n/2 times 1/n.
+    Also the adjoint identity <R2C x, g> = <x, R2C^T g> on the GPU's results."""
+    n = 1 << lg
+    h = n // 2
+    batch = batch_for(n)
+    p = gb.get_plan("r2c", (n,), batch)
+    g = half_spectrum(n, batch, seed=6700 + lg)           # nonzero Im g[0], Im g[n/2] must not enter
+    gt = torch.from_numpy(g).cuda()
+    y = torch.empty(batch, n, dtype=torch.float32, device="cuda")
+    p.exec_ptr(gt.data_ptr(), y.data_ptr(), L.FFT_ADJOINT)
+    pad = np.zeros((batch, n), complex)
+    pad[:, : h + 1] = g.astype(np.complex128)
+    ref = oracle.transform(pad, oracle.ADJOINT).real
+    yh = y.cpu().numpy()
+    assert oracle.rel_l2_rows(yh, ref).max() <= tol(n), f"R2C adjoint N=2^{lg}"
+
+    r = real_rows(n, batch, seed=6800 + lg)
+    rt = torch.from_numpy(r).cuda()
+    c = torch.empty(batch, h + 1, dtype=torch.complex64, device="cuda")
+    p.exec_ptr(rt.data_ptr(), c.data_ptr(), L.FFT_INVERSE | L.FFT_ADJOINT)
+    wts = np.full(h + 1, 2.0 / n)
+    wts[0] = wts[h] = 1.0 / n
+    ref2 = oracle.rfft(r.astype(np.float64)) * wts
+    assert oracle.rel_l2_rows(c.cpu().numpy(), ref2).max() <= tol(n), f"C2R adjoint N=2^{lg}"
+
+    # <R2C r, g>_R = <r, R2C^T g>: both sides from the GPU's own outputs
+    X = gb.rfft(rt).cpu().numpy().astype(np.complex128)
+    lhs = np.sum((np.conj(X) * g.astype(np.complex128)).real, axis=-1)
+    rhs = np.sum(r.astype(np.float64) * yh.astype(np.float64), axis=-1)
+    scale = np.linalg.norm(X, axis=-1) * np.linalg.norm(g, axis=-1)
+    assert np.max(np.abs(lhs - rhs) / scale) <= tol(n)
+
+
 def test_real_plan_errors():
     lib = L.load()
     p = gb.get_plan("r2c", (1024,), 2)
@@ -145,7 +184,8 @@ def test_real_plan_errors():
     e = torch.zeros(4096, dtype=torch.complex64, device="cuda")
     nul = ctypes.c_void_p(0)
     dp, ep = ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(e.data_ptr())
-    assert lib.fft_exec_dir(p.handle, dp, ep, 2, nul) == -1            # adjoint directions: not for real data
+    assert lib.fft_exec_dir(p.handle, dp, ep, 4, nul) == -1            # no such direction
+    assert lib.fft_exec_dir(p.handle, dp, dp, 2, nul) == -1            # adjoint, in place
     assert lib.fft_exec_dir(p.handle, dp, dp, 0, nul) == -1            # in place
     assert lib.fft_exec_dir(p.handle, ctypes.c_void_p(d.data_ptr() + 4), ep, 0, nul) == -2
     assert lib.fft_plan_kind(p.handle) == 4
