@@ -424,7 +424,8 @@ def measure_other_configs(torch, lib, dev, stream, peak, iters, warmup):
     wh = workloads.real_weights(total, seed=workloads.seed_for(4, 1))
     x = torch.from_numpy(xh).to(dev)
     w2 = torch.from_numpy(2.0 * wh.astype(np.float32) ** 2).to(dev)
-    pm = api.Plan("many", (total,), len(lengths), 0, "fp32", dev, lengths=lengths)
+    mcfg = tune.tuned_many_config(lengths, dev)   # the autotuner's configuration (shipped or cached)
+    pm = api.Plan("many", (total,), len(lengths), 0, "fp32", dev, lengths=lengths, config=mcfg)
     X, G, gx = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
 
     def step():
@@ -440,6 +441,11 @@ def measure_other_configs(torch, lib, dev, stream, peak, iters, warmup):
         step()
     ms_step = _time_fn(torch, g.replay, iters, warmup, stream)
     ms_fwd = _time_fn(torch, lambda: pm.exec_ptr(x.data_ptr(), X.data_ptr(), 0, stream), iters, warmup, stream)
+    pd = api.Plan("many", (total,), len(lengths), 0, "fp32", dev, lengths=lengths)   # planner defaults
+    ms_fwd_default = _time_fn(torch, lambda: pd.exec_ptr(x.data_ptr(), G.data_ptr(), 0, stream), iters, warmup,
+                              stream)
+    default_cfg = pd.many_config()
+    pd.close()
     fl = sum(flops(nn, 1) for nn in lengths)
     gxh = gx.cpu().numpy()
     offs = np.concatenate([[0], np.cumsum(lengths)])
@@ -454,7 +460,10 @@ def measure_other_configs(torch, lib, dev, stream, peak, iters, warmup):
                           "graph_step_us": round(ms_step * 1e3, 1),
                           "gflops_fwd_plus_bwd": round(2 * fl / (ms_step * 1e-3) / 1e9, 1),
                           "grad_rel_l2_max_sampled": float(f"{max(errs):.3e}"), "grad_samples": len(errs),
-                          "step": "graph-captured: forward (one launch), 2 w^2 X (torch), adjoint (one launch)"}
+                          "step": "graph-captured: forward (one launch), 2 w^2 X (torch), adjoint (one launch)",
+                          "plan_config": pm.many_config(),
+                          "forward_us_planner_default": round(ms_fwd_default * 1e3, 1),
+                          "planner_default_config": default_cfg}
     pm.close()
     return out
 
@@ -924,7 +933,7 @@ def run_measure(args):
         wh = workloads.real_weights(total, seed=workloads.seed_for(4, 1))
         x = torch.from_numpy(xh).to(dev)
         w2 = torch.from_numpy(2.0 * wh.astype(np.float32) ** 2).to(dev)
-        p = api.get_plan("many", (total,), len(lengths), "fp32", dev, lengths=tuple(lengths))
+        p = api.get_plan("many", (total,), len(lengths), "fp32", dev, lengths=tuple(lengths), tuned=True)
         X = torch.empty_like(x)
         G = torch.empty_like(x)
         gx = torch.empty_like(x)

@@ -137,6 +137,47 @@ GBFFT_API fft_plan* fft_plan_create_r2c(int64_t n, int64_t batch, int prec);
  * the lengths before it.  The host array is copied; the caller keeps it. */
 GBFFT_API fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, int prec);
 
+/* Configuration of an uneven-batch plan (the knobs of fft_autotune_many).  The
+ * plan runs as one persistent launch over a queue of tiles of at most 4096
+ * points: batch tiles of equal-length transforms up to 2^12, and the column
+ * and row tiles of a four-step split N = N1 * N2 (Sec. 2.3.2) for 2^13..2^16.
+ *   gap:         the row tiles of a four-step transform are queued this many
+ *                half resident grids after its column tiles (1..16; <= 0 =
+ *                default 4).  Short gaps keep the intermediate in L2 but make
+ *                row tiles wait; long gaps do the opposite.
+ *   ctas_per_sm: resident CTAs per SM of the persistent launch (<= 0 = the
+ *                occupancy limit of the kernel, 4; larger values are lowered
+ *                to that limit).
+ *   lg1[i]:      log2 N1 of the split for transforms of length 2^(13+i):
+ *                2^13: 7, 2^14: 7 or 8, 2^15: 7 or 8, 2^16: 8
+ *                (<= 0 = defaults 7, 7, 8, 8).  Other values are invalid. */
+typedef struct fft_many_config {
+  int gap, ctas_per_sm;
+  int lg1[4];
+} fft_many_config;
+
+/* As fft_plan_create_many, with an explicit configuration (NULL = defaults).
+ * NULL with FFT_ERR_INVALID_ARG for a configuration outside the ranges above. */
+GBFFT_API fft_plan* fft_plan_create_many_config(const int64_t* lengths, int64_t count, int dir, int prec,
+                                                const fft_many_config* cfg);
+
+/* The resolved configuration of an uneven-batch plan (FFT_ERR_INVALID_ARG for
+ * other plan kinds). */
+GBFFT_API int fft_plan_get_many_config(const fft_plan* plan, fft_many_config* out);
+
+/* Autotuner of uneven-batch plans: builds the plan for (lengths, count, prec)
+ * under every configuration of the search space -- gap in {1, 2, 3, 4, 6, 8},
+ * CTAs per SM from 2 to the occupancy limit, and every valid split for each
+ * four-step length that occurs in `lengths` -- times each with CUDA events
+ * over `iters` executions (after 3 untimed ones) on the caller's device
+ * buffers in/out (the packed data, sum(lengths) complex64 each) and workspace
+ * ws of ws_bytes (>= the plan's fft_plan_workspace_bytes), and writes the
+ * fastest configuration to *best and its mean time in microseconds to
+ * *best_us.  Synchronises `stream`; overwrites the buffers; creates plans, so
+ * call it outside any stream capture.  FP32 only. */
+GBFFT_API int fft_autotune_many(const int64_t* lengths, int64_t count, int prec, void* in, void* out, void* ws,
+                                size_t ws_bytes, void* stream, int iters, fft_many_config* best, float* best_us);
+
 /* Runs the plan on `stream` (a cudaStream_t; NULL = legacy default stream)
  * in the plan's direction.  Asynchronous: returns once the launches are
  * queued.  in/out: the packed data (complex64; complex128 for FFT_PREC_FP64;

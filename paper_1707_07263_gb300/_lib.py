@@ -44,6 +44,23 @@ class FftPlanConfig(ctypes.Structure):
         return c
 
 
+class FftManyConfig(ctypes.Structure):
+    """fft_many_config of include/gbfft.h (uneven-batch plans)."""
+    _fields_ = [("gap", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("lg1", ctypes.c_int * 4)]
+
+    def as_dict(self) -> dict:
+        return {"gap": int(self.gap), "ctas_per_sm": int(self.ctas_per_sm), "lg1": [int(v) for v in self.lg1]}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "FftManyConfig":
+        c = cls()
+        c.gap = int(d.get("gap", 0))
+        c.ctas_per_sm = int(d.get("ctas_per_sm", 0))
+        for i, v in enumerate(d.get("lg1", [0, 0, 0, 0])):
+            c.lg1[i] = int(v)
+        return c
+
+
 # name -> (restype, argtypes); the full exported surface of include/gbfft.h
 _i64, _int, _vp, _sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
 SIGNATURES = {
@@ -51,6 +68,10 @@ SIGNATURES = {
     "fft_plan_create_2d": (_vp, [_i64, _i64, _i64, _int, _int]),
     "fft_plan_create_many": (_vp, [ctypes.POINTER(_i64), _i64, _int, _int]),
     "fft_plan_create_r2c": (_vp, [_i64, _i64, _int]),
+    "fft_plan_create_many_config": (_vp, [ctypes.POINTER(_i64), _i64, _int, _int, ctypes.POINTER(FftManyConfig)]),
+    "fft_plan_get_many_config": (_int, [_vp, ctypes.POINTER(FftManyConfig)]),
+    "fft_autotune_many": (_int, [ctypes.POINTER(_i64), _i64, _int, _vp, _vp, _vp, _sz, _vp, _int,
+                                 ctypes.POINTER(FftManyConfig), ctypes.POINTER(ctypes.c_float)]),
     "fft_exec": (_int, [_vp, _vp, _vp, _vp]),
     "fft_exec_dir": (_int, [_vp, _vp, _vp, _int, _vp]),
     "fft_destroy": (None, [_vp]),

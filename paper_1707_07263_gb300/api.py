@@ -69,7 +69,11 @@ class Plan:
             elif kind == "many":
                 arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
                 self.lengths = [int(v) for v in lengths]
-                h = self.lib.fft_plan_create_many(arr, len(lengths), self.dir, self.prec)
+                if config is not None:
+                    mc = L.FftManyConfig.from_dict(config)
+                    h = self.lib.fft_plan_create_many_config(arr, len(lengths), self.dir, self.prec, ctypes.byref(mc))
+                else:
+                    h = self.lib.fft_plan_create_many(arr, len(lengths), self.dir, self.prec)
             else:
                 raise ValueError(kind)
             if not h:
@@ -87,6 +91,12 @@ class Plan:
     @property
     def launches(self) -> int:
         return int(self.lib.fft_plan_launches(self.handle))
+
+    def many_config(self) -> dict:
+        """Resolved configuration of an uneven-batch plan."""
+        c = L.FftManyConfig()
+        L.check(self.lib.fft_plan_get_many_config(self.handle, ctypes.byref(c)), "fft_plan_get_many_config")
+        return c.as_dict()
 
     def describe(self) -> str:
         buf = ctypes.create_string_buffer(512)
@@ -154,11 +164,12 @@ _cache_lock = threading.Lock()
 
 def get_plan(kind: str, shape, batch: int, prec="fp32", device=None, lengths=None, tuned: bool = False) -> Plan:
     """Cached plan (twiddle tables are built once per shape/precision/device).
-    tuned=True builds 1-D plans from the autotuner's cached configuration
-    (tuning the shape first if it has never been tuned on this GPU model)."""
+    tuned=True builds 1-D and uneven-batch plans from the autotuner's cached
+    configuration (tuning the shape first if it has never been tuned on this
+    GPU model)."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     key = (kind, tuple(shape), int(batch), _prec_code(prec), dev.index,
-           tuple(lengths) if lengths is not None else None, bool(tuned and kind == "1d"))
+           tuple(lengths) if lengths is not None else None, bool(tuned and kind in ("1d", "many")))
     with _cache_lock:
         p = _cache.get(key)
         if p is None:
@@ -168,6 +179,9 @@ def get_plan(kind: str, shape, batch: int, prec="fp32", device=None, lengths=Non
             if tuned and kind == "1d" and tunable:   # mixed-radix and FP64 plans take no configuration
                 from . import tune
                 config = tune.tuned_config(int(shape[0]), int(batch), _prec_code(prec), dev)
+            elif tuned and kind == "many" and _prec_code(prec) == L.FFT_PREC_FP32:
+                from . import tune
+                config = tune.tuned_many_config(lengths, dev)
             p = Plan(kind, shape, batch, FORWARD, prec, dev, lengths, config=config)
             _cache[key] = p
         return p
@@ -228,14 +242,15 @@ class _FFT2d(torch.autograd.Function):
 
 class _FFTMany(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, lengths, dir, prec):
-        plan = get_plan("many", (int(sum(lengths)),), len(lengths), prec, x.device, lengths=tuple(lengths))
+    def forward(ctx, x, lengths, dir, prec, tuned):
+        plan = get_plan("many", (int(sum(lengths)),), len(lengths), prec, x.device, lengths=tuple(lengths),
+                        tuned=tuned)
         ctx.plan, ctx.dir = plan, dir
         return plan(x, dir=dir)
 
     @staticmethod
     def backward(ctx, g):
-        return ctx.plan(g.contiguous(), dir=ctx.dir ^ ADJOINT), None, None, None
+        return ctx.plan(g.contiguous(), dir=ctx.dir ^ ADJOINT), None, None, None, None
 
 
 def _prec_for(x: torch.Tensor, prec):
@@ -271,16 +286,18 @@ def ifft2(x: torch.Tensor, prec="fp32") -> torch.Tensor:
     return _FFT2d.apply(x, INVERSE, prec)
 
 
-def fft_many(packed: torch.Tensor, lengths, inverse: bool = False, prec="fp32") -> torch.Tensor:
+def fft_many(packed: torch.Tensor, lengths, inverse: bool = False, prec="fp32", tuned: bool = False) -> torch.Tensor:
     """Transforms of uneven power-of-two lengths packed back to back in a 1-D
-    complex64 tensor (transform i starts at sum(lengths[:i]))."""
+    complex64 tensor (transform i starts at sum(lengths[:i])).  tuned=True
+    builds the plan from the autotuner's configuration for this length list on
+    this GPU model (cached per GPU model; tuned once, on first use)."""
     _check_input(packed)
     lengths = [int(v) for v in lengths]
     if packed.numel() != sum(lengths):
         raise ValueError("packed size does not match the sum of the lengths")
     if not lengths:
         return packed.reshape(-1).clone()
-    return _FFTMany.apply(packed.reshape(-1), lengths, INVERSE if inverse else FORWARD, prec)
+    return _FFTMany.apply(packed.reshape(-1), lengths, INVERSE if inverse else FORWARD, prec, bool(tuned))
 
 
 def _run_filter(x: torch.Tensor, H: torch.Tensor, dir: int = FORWARD) -> torch.Tensor:

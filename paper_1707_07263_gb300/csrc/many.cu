@@ -72,6 +72,7 @@ struct ManyArgs {
 };
 
 struct ManyPlan {
+  fft_many_config cfg{};   // resolved configuration
   void* d_mem = nullptr;   // items, transforms, offsets, tables, counters
   size_t counters_bytes = 0;
   int* d_counters = nullptr;
@@ -83,9 +84,16 @@ struct ManyPlan {
 
 constexpr int kManyThreads = 256;
 
-// the four-step split used for 2^13..2^16 inside the persistent kernel
-__host__ __device__ constexpr int many_lg1(int lgN) { return lgN <= 14 ? 7 : 8; }
-__host__ __device__ constexpr int many_lg2(int lgN) { return lgN - many_lg1(lgN); }
+// The four-step split of 2^13..2^16 inside the persistent kernel: column
+// tiles of length 2^lg1 (32 or 16 columns; lg1 = 7, 8) and row tiles of length
+// 2^(lgN - lg1) (lengths 2^6..2^8).  Default lg1: 7, 7, 8, 8.  (A 64-column
+// tile of 2^6 would raise the kernel's shared memory from 41.5 to 49.7 KB per
+// CTA, taking a third of the L1 that caches the twiddle tables at four CTAs
+// per SM: measured 14 % slower on the 4096-transform batch.)
+constexpr int many_default_lg1(int lgN) { return lgN <= 14 ? 7 : 8; }
+constexpr bool many_split_ok(int lgN, int lg1) { return lg1 >= 7 && lg1 <= 8 && lgN - lg1 >= 6 && lgN - lg1 <= 8; }
+constexpr int kManyDefaultGap = 4;   // half resident grids between column and row tiles
+constexpr int kManyMaxGap = 16;
 
 template <int LG, int C, bool ICF, bool OCF>
 constexpr int many_smem() { return TileCfg<LG, C, ICF, OCF>::SMEM_BYTES; }
@@ -257,8 +265,31 @@ static bool fault_missing_producer() {
 static bool fault_missing_producer() { return false; }
 #endif
 
-int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
+// Resolves a configuration against the defaults; FFT_ERR_INVALID_ARG if a
+// field is out of range.  ctas_per_sm is lowered to `occupancy` later.
+int many_resolve_config(const fft_many_config* in, fft_many_config* out) {
+  fft_many_config c{};
+  c.gap = kManyDefaultGap;
+  c.ctas_per_sm = 0;
+  for (int i = 0; i < 4; ++i) c.lg1[i] = many_default_lg1(13 + i);
+  if (in) {
+    if (in->gap > kManyMaxGap) return FFT_ERR_INVALID_ARG;
+    if (in->gap > 0) c.gap = in->gap;
+    if (in->ctas_per_sm > 0) c.ctas_per_sm = in->ctas_per_sm;
+    for (int i = 0; i < 4; ++i) {
+      if (in->lg1[i] <= 0) continue;
+      if (!many_split_ok(13 + i, in->lg1[i])) return FFT_ERR_INVALID_ARG;
+      c.lg1[i] = in->lg1[i];
+    }
+  }
+  *out = c;
+  return FFT_OK;
+}
+
+int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count, const fft_many_config* cfg_in) {
   if (count > (1 << 24)) return FFT_ERR_INVALID_ARG;
+  fft_many_config cfg;
+  if (many_resolve_config(cfg_in, &cfg) != FFT_OK) return FFT_ERR_INVALID_ARG;
   std::vector<int> lg(count);
   long long total = 0;
   for (int64_t i = 0; i < count; ++i) {
@@ -306,11 +337,11 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, many_kernel, kManyThreads, kManySmem) != cudaSuccess ||
       per_sm < 1)
     return FFT_ERR_CUDA;
-  const size_t resident = (size_t)per_sm * (size_t)sms;
+  cfg.ctas_per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, per_sm) : per_sm;
+  const size_t resident = (size_t)cfg.ctas_per_sm * (size_t)sms;
   // items queued between a transform's column and row tiles (in units of
-  // half the resident grid; GBFFT_MANY_GAP overrides the default of 4)
-  const char* gap_env = getenv("GBFFT_MANY_GAP");
-  const size_t gap = (size_t)std::max(1, gap_env ? atoi(gap_env) : 4) * resident / 2;
+  // half the resident grid)
+  const size_t gap = (size_t)cfg.gap * resident / 2;
 
   // four-step transforms, largest first: column tiles in order, each
   // transform's row tiles once `gap` more items have been queued
@@ -324,8 +355,8 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
       t.off = off[i];
       t.ws_off = ws_total;
       t.lgN = L;
-      t.lg1 = many_lg1(L);
-      t.lg2 = many_lg2(L);
+      t.lg1 = cfg.lg1[L - 13];
+      t.lg2 = L - t.lg1;
       t.c1 = 4096 >> t.lg1;
       t.c2 = 4096 >> t.lg2;
       ws_total += 1LL << L;
@@ -377,6 +408,7 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
   ManyPlan* mp = new (std::nothrow) ManyPlan;
   if (!mp) return FFT_ERR_ALLOC;
   p->many = mp;
+  mp->cfg = cfg;
   const size_t b_items = al256(sizeof(ManyItem) * (items.size() + 1));
   const size_t b_trs = al256(sizeof(ManyTransform) * (trs.size() + 1));
   const size_t b_slots = al256(sizeof(long long) * (slots.size() + 1));
@@ -441,6 +473,12 @@ int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count) {
   p->n = total;
   p->ws_bytes = (size_t)ws_total * 8;
   p->launches = 1;
+  return FFT_OK;
+}
+
+int many_get_config(const fft_plan* p, fft_many_config* out) {
+  if (!p->many) return FFT_ERR_INVALID_ARG;
+  *out = p->many->cfg;
   return FFT_OK;
 }
 

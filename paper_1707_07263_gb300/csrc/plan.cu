@@ -31,7 +31,9 @@ using namespace gbfft;
 namespace gbfft {
 
 // defined in many.cu / tc.cu
-int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count);
+int many_plan_init(fft_plan* p, const int64_t* lengths, int64_t count, const fft_many_config* cfg);
+int many_get_config(const fft_plan* p, fft_many_config* out);
+int many_resolve_config(const fft_many_config* in, fft_many_config* out);
 void many_plan_free(fft_plan* p);
 int many_exec(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s);
 int tc_plan_init(fft_plan* p);
@@ -1201,7 +1203,18 @@ fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int
 }
 
 fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, int prec) {
-  if (!lengths || count < 1 || !valid_dir(dir) || !valid_prec(prec)) {
+  return fft_plan_create_many_config(lengths, count, dir, prec, nullptr);
+}
+
+int fft_plan_get_many_config(const fft_plan* plan, fft_many_config* out) {
+  if (!is_live(plan) || !out || plan->kind != KIND_MANY) return set_err(FFT_ERR_INVALID_ARG);
+  return set_err(many_get_config(plan, out));
+}
+
+fft_plan* fft_plan_create_many_config(const int64_t* lengths, int64_t count, int dir, int prec,
+                                      const fft_many_config* cfg) {
+  fft_many_config resolved;
+  if (!lengths || count < 1 || !valid_dir(dir) || !valid_prec(prec) || many_resolve_config(cfg, &resolved) != FFT_OK) {
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
   }
@@ -1223,7 +1236,7 @@ fft_plan* fft_plan_create_many(const int64_t* lengths, int64_t count, int dir, i
   p->dir = dir;
   p->prec = prec;
   p->batch = count;
-  int rc = many_plan_init(p, lengths, count);
+  int rc = many_plan_init(p, lengths, count, cfg);
   if (rc != FFT_OK) {
     free_plan(p);
     set_err(rc);

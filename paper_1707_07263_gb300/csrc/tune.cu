@@ -153,3 +153,88 @@ extern "C" GBFFT_API int fft_autotune(int64_t n, int64_t batch, int prec, void* 
   *best_us = best_t;
   return FFT_OK;
 }
+
+// Uneven batches: the queue gap, the resident CTAs per SM and the split of every
+// four-step length present (fft_many_config).  The paper's thresholds for
+// splitting a transform are fixed by hand (Sec. 2.3.2, Sec. 3); here they are
+// timed on the batch at hand, one persistent launch per candidate.
+extern "C" GBFFT_API int fft_autotune_many(const int64_t* lengths, int64_t count, int prec, void* in, void* out,
+                                           void* ws, size_t ws_bytes, void* stream, int iters, fft_many_config* best,
+                                           float* best_us) {
+  if (!lengths || count < 1 || !in || !out || !best || !best_us || iters < 1) return set_err(FFT_ERR_INVALID_ARG);
+  if (prec != FFT_PREC_FP32) return set_err(FFT_ERR_UNSUPPORTED);
+  bool present[4] = {false, false, false, false};
+  for (int64_t i = 0; i < count; ++i)
+    for (int L = 13; L <= 16; ++L)
+      if (lengths[i] == (1LL << L)) present[L - 13] = true;
+  // splits: every valid lg1 for the four-step lengths present, the default otherwise
+  std::vector<std::vector<int>> opts(4);
+  for (int i = 0; i < 4; ++i) {
+    const int L = 13 + i;
+    if (present[i]) {
+      for (int lg1 = 7; lg1 <= 8; ++lg1)
+        if (L - lg1 >= 6 && L - lg1 <= 8) opts[i].push_back(lg1);
+    } else {
+      opts[i].push_back(0);
+    }
+  }
+  std::vector<fft_many_config> cands;
+  const int gaps[] = {1, 2, 3, 4, 6, 8};
+  for (int g : gaps)
+    for (int ctas = 2; ctas <= 4; ++ctas)
+      for (int a : opts[0])
+        for (int b : opts[1])
+          for (int c : opts[2])
+            for (int d : opts[3]) {
+              fft_many_config cf;
+              memset(&cf, 0, sizeof(cf));
+              cf.gap = g;
+              cf.ctas_per_sm = ctas;
+              cf.lg1[0] = a;
+              cf.lg1[1] = b;
+              cf.lg1[2] = c;
+              cf.lg1[3] = d;
+              cands.push_back(cf);
+            }
+  fft_many_config dflt;
+  memset(&dflt, 0, sizeof(dflt));
+  cands.insert(cands.begin(), dflt);   // the planner's default is always a candidate
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return set_err(FFT_ERR_CUDA);
+  float best_t = 1e30f;
+  bool found = false;
+  for (const fft_many_config& c : cands) {
+    fft_plan* p = fft_plan_create_many_config(lengths, count, FFT_FORWARD, prec, &c);
+    if (!p) continue;
+    const size_t need = fft_plan_workspace_bytes(p);
+    if (need && (!ws || ws_bytes < need)) {
+      fft_destroy(p);
+      continue;
+    }
+    if (need) fft_plan_set_workspace(p, ws);
+    bool ok = true;
+    for (int w = 0; w < 3 && ok; ++w) ok = fft_exec(p, in, out, stream) == FFT_OK;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < iters && ok; ++i) ok = fft_exec(p, in, out, stream) == FFT_OK;
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ok = false;
+    if (ok && fft_status(p, stream) != FFT_OK) ok = false;   // a bounded wait ran out: not a valid candidate
+    if (ok) {
+      const float t = ms * 1000.f / iters;
+      if (t < best_t) {
+        best_t = t;
+        fft_plan_get_many_config(p, best);
+        found = true;
+      }
+    }
+    fft_destroy(p);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (!found) return set_err(FFT_ERR_UNSUPPORTED);
+  *best_us = best_t;
+  return FFT_OK;
+}

@@ -87,6 +87,28 @@ def test_plan_create_many_rejects(lib):
     assert lib.fft_last_error() == -1
 
 
+def test_plan_create_many_config_rejects(lib):
+    """Out-of-range uneven-batch configurations fail before anything runs."""
+    from paper_1707_07263_gb300 import _lib
+    arr = (ctypes.c_int64 * 3)(1 << 13, 1 << 16, 256)
+    bad = [{"gap": 17}, {"lg1": [8, 0, 0, 0]}, {"lg1": [6, 0, 0, 0]}, {"lg1": [0, 6, 0, 0]}, {"lg1": [0, 9, 0, 0]},
+           {"lg1": [0, 0, 6, 0]}, {"lg1": [0, 0, 0, 7]}, {"lg1": [0, 0, 0, 9]}]
+    for d in bad:
+        c = _lib.FftManyConfig.from_dict(d)
+        assert lib.fft_plan_create_many_config(arr, 3, 0, 0, ctypes.byref(c)) is None, d
+        assert lib.fft_last_error() == -1
+    c = _lib.FftManyConfig()
+    assert lib.fft_plan_create_many_config(None, 3, 0, 0, ctypes.byref(c)) is None
+    assert lib.fft_plan_get_many_config(None, ctypes.byref(c)) == -1
+    us = ctypes.c_float()
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.fft_autotune_many(None, 3, 0, p, p, p, 64, None, 5, ctypes.byref(c), ctypes.byref(us)) == -1
+    assert lib.fft_autotune_many(arr, 3, 0, p, p, p, 64, None, 0, ctypes.byref(c), ctypes.byref(us)) == -1
+    assert lib.fft_autotune_many(arr, 0, 0, p, p, p, 64, None, 5, ctypes.byref(c), ctypes.byref(us)) == -1
+    assert lib.fft_autotune_many(arr, 3, 1, p, p, p, 64, None, 5, ctypes.byref(c), ctypes.byref(us)) == -6
+
+
 def test_plan_create_r2c_rejects(lib):
     assert lib.fft_plan_create_r2c(12, 1, 0) is None      # not a power of two
     assert lib.fft_plan_create_r2c(2, 1, 0) is None       # below 4

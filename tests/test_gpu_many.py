@@ -183,3 +183,61 @@ def test_many_config5_full_shape_forward_and_graph_gradient(lib):
         err = oracle.rel_l2(got[o:o + n], ref)
         assert err <= 1e-6 * np.log2(n), f"gradient, length {n} at {o}: {err:.3e}"
         o += n
+
+
+@pytest.mark.parametrize("cfg", [{"gap": 1, "ctas_per_sm": 2, "lg1": [7, 8, 7, 8]},
+                                 {"gap": 8, "ctas_per_sm": 3, "lg1": [7, 8, 8, 8]},
+                                 {"gap": 3, "ctas_per_sm": 9, "lg1": [0, 0, 0, 0]}])
+def test_many_explicit_configs(lib, cfg):
+    """Every split the configuration offers, short and long gaps, fewer
+    resident CTAs (and a count above the occupancy limit, which is lowered),
+    against the oracle for every transform and direction."""
+    lengths = [1 << e for e in (13, 14, 15, 16, 9, 14, 13, 12, 16, 15, 1)] * 3
+    arr = (ctypes.c_int64 * len(lengths))(*lengths)
+    c = _lib.FftManyConfig.from_dict(cfg)
+    for d in (0, 1):
+        h = lib.fft_plan_create_many_config(arr, len(lengths), d, 0, ctypes.byref(c))
+        assert h, _lib.ERRORS.get(lib.fft_last_error())
+        got_cfg = _lib.FftManyConfig()
+        assert lib.fft_plan_get_many_config(ctypes.c_void_p(h), ctypes.byref(got_cfg)) == 0
+        res = got_cfg.as_dict()
+        assert 1 <= res["ctas_per_sm"] <= min(max(cfg["ctas_per_sm"], 1), 4)
+        for i, v in enumerate(cfg["lg1"]):
+            assert res["lg1"][i] == (v if v > 0 else (7, 7, 8, 8)[i])
+        lib.fft_destroy(ctypes.c_void_p(h))
+        p = ManyPlanCfg(lib, lengths, d, c)
+        x = workloads.packed_cgauss(lengths, seed=800 + d)
+        got = p.run(torch.from_numpy(x).cuda(), d).cpu().numpy()
+        check(got, oracle_many(x, lengths, d), lengths, f"config {cfg} dir {d}")
+        assert p.status() == 0
+
+
+class ManyPlanCfg(ManyPlan):
+    def __init__(self, lib, lengths, d, cfg):
+        arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
+        h = lib.fft_plan_create_many_config(arr, len(lengths), d, 0, ctypes.byref(cfg))
+        assert h, _lib.ERRORS.get(lib.fft_last_error())
+        self.lib, self.h = lib, ctypes.c_void_p(h)
+        ws = lib.fft_plan_workspace_bytes(self.h)
+        self.ws = torch.empty(max(ws, 256), dtype=torch.uint8, device="cuda")
+        if ws:
+            assert lib.fft_plan_set_workspace(self.h, ctypes.c_void_p(self.ws.data_ptr())) == 0
+
+
+def test_many_autotuned_plan_matches_oracle(lib, tmp_path, monkeypatch):
+    """The native search over uneven-batch configurations returns a valid
+    configuration, the tuned plan (built through the per-GPU cache) matches
+    the oracle on every transform, and the result is cached."""
+    monkeypatch.setenv("GBFFT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_1707_07263_gb300 import api, tune
+    lengths = workloads.uneven_lengths(512, seed=workloads.seed_for(4, 7)).tolist()
+    cfg = tune.tuned_many_config(lengths, torch.device("cuda", 0))
+    assert set(cfg) == {"gap", "ctas_per_sm", "lg1"} and 1 <= cfg["gap"] <= 16
+    assert (tmp_path / "tune.json").exists()
+    assert tune.tuned_many_config(lengths, torch.device("cuda", 0)) == cfg     # from the cache now
+    x = workloads.packed_cgauss(lengths, seed=901)
+    xt = torch.from_numpy(x).cuda()
+    got = api.fft_many(xt, lengths, tuned=True).cpu().numpy()
+    check(got, oracle_many(x, lengths, 0), lengths, f"tuned {cfg}")
+    back = api.fft_many(torch.from_numpy(got).cuda(), lengths, inverse=True, tuned=True).cpu().numpy()
+    assert oracle.rel_l2(back, x) <= 2 * 5e-7 * 16
