@@ -3,11 +3,12 @@
 Each translation unit is compiled in parallel; the shared library links the
 CUDA runtime statically so it loads without extra library paths.
 
-Beside it, the same objects with ``many.cu`` recompiled under
-``-DGBFFT_FAULT_INJECTION`` are linked into ``libgbfft_faultinject.so``, a
-test-only library in which an environment switch plants a missing producer in
-an uneven-batch plan (the bounded-wait timeout test).  The product library
-has no such switch.
+Beside it, the same objects with the planner sources recompiled under
+``-DGBFFT_TEST_HOOKS`` are linked into ``libgbfft_testhooks.so``, a test-only
+library in which environment variables force planner choices (passes,
+splits, staging kernels, tile sizes) and plant a missing producer in an
+uneven-batch plan (the bounded-wait timeout test).  The product library reads
+no environment variable.
 """
 from __future__ import annotations
 
@@ -22,9 +23,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbfft.so")
-FAULT_LIB = os.path.join(HERE, "libgbfft_faultinject.so")
-FAULT_SRC = "many.cu"          # the one source whose fault-injection build differs
-FAULT_FLAGS = ["-DGBFFT_FAULT_INJECTION"]
+TEST_LIB = os.path.join(HERE, "libgbfft_testhooks.so")
+TEST_SRCS = ("many.cu", "mixed.cu", "plan.cu")   # the sources whose test build differs
+TEST_FLAGS = ["-DGBFFT_TEST_HOOKS"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
@@ -67,11 +68,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
     dep_mtime = max(os.path.getmtime(p) for p in _deps())
-    fault_src = os.path.join(CSRC, FAULT_SRC)
-    fault_obj = os.path.join(BUILD, FAULT_SRC[:-3] + "_faultinject.o")
+
+    def obj(src, test=False):
+        return os.path.join(BUILD, os.path.basename(src)[:-3] + ("_testhooks.o" if test else ".o"))
+
+    units = [(s, obj(s), list(extra)) for s in srcs]
+    units += [(os.path.join(CSRC, t), obj(t, True), list(extra) + TEST_FLAGS) for t in TEST_SRCS]
     jobs = []
-    for s, o, flags in [(s, os.path.join(BUILD, os.path.basename(s)[:-3] + ".o"), list(extra)) for s in srcs] + \
-            [(fault_src, fault_obj, list(extra) + FAULT_FLAGS)]:
+    for s, o, flags in units:
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), dep_mtime):
             jobs.append((s, o, flags))
     if jobs:
@@ -82,11 +86,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 msg = f.result()
                 if verbose and msg:
                     sys.stderr.write(msg)
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [obj(s) for s in srcs]
     if force or jobs or not os.path.exists(LIB):
         _link(LIB, objs)
-    if force or jobs or not os.path.exists(FAULT_LIB):
-        _link(FAULT_LIB, [fault_obj if os.path.basename(o) == FAULT_SRC[:-3] + ".o" else o for o in objs])
+    if force or jobs or not os.path.exists(TEST_LIB):
+        _link(TEST_LIB, [obj(s, os.path.basename(s) in TEST_SRCS) for s in srcs])
     return LIB
 
 

@@ -251,12 +251,12 @@ __global__ void __launch_bounds__(kManyThreads, 4) many_kernel(const ManyArgs m)
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Fault injection for the bounded-wait test, compiled only into the test
-// library libgbfft_faultinject.so (nvcc -DGBFFT_FAULT_INJECTION); the product
+// library libgbfft_testhooks.so (nvcc -DGBFFT_TEST_HOOKS); the product
 // library libgbfft.so has no such switch.  In the test library, a plan created
 // while GBFFT_FAULT_MISSING_PRODUCER=1 is set gets one row tile that waits for
 // a column tile that does not exist, with a ~1 ms wait budget, so the timeout
 // path is exercised without any GPU fault.
-#ifdef GBFFT_FAULT_INJECTION
+#ifdef GBFFT_TEST_HOOKS
 static bool fault_missing_producer() {
   const char* e = getenv("GBFFT_FAULT_MISSING_PRODUCER");
   return e && atoi(e) != 0;

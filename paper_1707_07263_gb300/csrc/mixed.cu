@@ -357,10 +357,11 @@ int mixed_plan_init(fft_plan* p) {
   const bool fp64 = p->prec == FFT_PREC_FP64;
   const size_t esz = fp64 ? 16 : 8;
   // points per CTA when several transforms share one, and the CTA size for
-  // such tiles (GBFFT_MIXED_TILE / GBFFT_MIXED_THREADS override the FP32
-  // values for measurement)
+  // such tiles (in the test build of the library, GBFFT_MIXED_TILE /
+  // GBFFT_MIXED_THREADS override the FP32 values for measurement)
   long long tile = fp64 ? 2048 : 4096;
   int small_threads = 256;
+#ifdef GBFFT_TEST_HOOKS
   if (!fp64) {
     const char* et = getenv("GBFFT_MIXED_TILE");
     const char* eh = getenv("GBFFT_MIXED_THREADS");
@@ -369,6 +370,7 @@ int mixed_plan_init(fft_plan* p) {
     if (t >= 256 && t <= 8192) tile = t;
     if (h == 128 || h == 256 || h == 512) small_threads = h;
   }
+#endif
   a.nrad = mixed_radices(N, a.rad);
   if (a.nrad == 0 || N > (fp64 ? kMixedMaxN64 : kMixedMaxN)) return FFT_ERR_UNSUPPORTED;
   a.N = (int)N;

@@ -73,10 +73,20 @@ static int ilog2_exact(int64_t v) {
   return l;
 }
 
+// Planner overrides for tests and measurements (which split, which staging
+// kernel, how many passes), read from the environment at plan creation.  Only
+// the test build of the library (libgbfft_testhooks.so, -DGBFFT_TEST_HOOKS)
+// reads them; in libgbfft.so every override is its default, so no variable of
+// the environment changes a production plan (fft_plan_config is the API for
+// choosing a configuration).
+#ifdef GBFFT_TEST_HOOKS
 static int env_int(const char* name, int dflt) {
   const char* s = getenv(name);
   return (s && *s) ? atoi(s) : dflt;
 }
+#else
+static int env_int(const char*, int dflt) { return dflt; }
+#endif
 
 static int prepare_kernel(const TileKernelInfo* k) {
   if (!k) return FFT_ERR_UNSUPPORTED;

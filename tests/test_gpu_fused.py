@@ -42,23 +42,23 @@ def run(lib, x: np.ndarray, d: int, inplace: bool = False):
 
 @pytest.mark.parametrize("lg", [13, 14, 15, 16, 17, 18])
 @pytest.mark.parametrize("batch", [1, 7, 40])
-def test_fused_forward_small_slabs(lib, monkeypatch, lg, batch):
-    # 1 MB slabs: many slabs per launch, both workspace slots reused
+def test_fused_forward_small_slabs(hooks_lib, monkeypatch, lg, batch):
+    # 1 MB slabs (a test-build override): many slabs per launch, both workspace slots reused
     monkeypatch.setenv("GBFFT_SLAB_MB", "1")
     n = 1 << lg
     x = workloads.cgauss(n, batch, seed=9000 + lg + batch)
-    got, st, ws = run(lib, x, 0)
+    got, st, ws = run(hooks_lib, x, 0)
     assert st == 0
     errs = oracle.rel_l2_rows(got, oracle.transform(x.astype(np.complex128)))
     assert errs.max() <= 5e-7 * lg
 
 
 @pytest.mark.parametrize("d", [1, 2, 3])
-def test_fused_directions_and_in_place(lib, monkeypatch, d):
+def test_fused_directions_and_in_place(hooks_lib, monkeypatch, d):
     monkeypatch.setenv("GBFFT_SLAB_MB", "2")
     n = 1 << 14
     x = workloads.uniform(n, 33, seed=9100 + d)
-    got, st, _ = run(lib, x, d, inplace=True)
+    got, st, _ = run(hooks_lib, x, d, inplace=True)
     assert st == 0
     x64 = x.astype(np.complex128)
     ref = {1: oracle.fft(x64, oracle.INVERSE), 2: oracle.fft(x64, oracle.ADJOINT),

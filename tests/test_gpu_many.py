@@ -118,10 +118,10 @@ def test_many_in_place_and_graph_replay(lib):
 def test_many_bounded_wait_reports_timeout(lib, monkeypatch):
     """A row tile told to wait for a column tile that never comes gives up
     after its budget and reports FFT_ERR_TIMEOUT instead of hanging.  The
-    missing producer is planted by the test-only fault-injection build of the
-    library (the product library has no such switch)."""
+    missing producer is planted by the test build of the library
+    (libgbfft_testhooks.so; the product library has no such switch)."""
     from paper_1707_07263_gb300 import build_lib
-    flib = _lib.load(build_lib.FAULT_LIB)
+    flib = _lib.load(build_lib.TEST_LIB)
     monkeypatch.setenv("GBFFT_FAULT_MISSING_PRODUCER", "1")
     lengths = [1 << 14, 1 << 10, 1 << 16]
     x = torch.from_numpy(workloads.packed_cgauss(lengths, seed=3)).cuda()

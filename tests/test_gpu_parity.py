@@ -102,13 +102,13 @@ def test_single_pass_directions(lib, lg, d):
 
 
 @pytest.mark.parametrize("lg", [3, 8, 10, 12, 13, 14])
-def test_single_pass_register_path(lib, monkeypatch, lg):
+def test_single_pass_register_path(hooks_lib, monkeypatch, lg):
     """The non-persistent kernel (no TMA staging) gives the same result."""
     monkeypatch.setenv("GBFFT_NO_TMA", "1")
     monkeypatch.setenv("GBFFT_HALVES", "1")
     n = 1 << lg
     x = workloads.cgauss(n, 11, seed=6000 + lg)
-    got = run_1d(lib, x, 1)
+    got = run_1d(hooks_lib, x, 1)
     assert_rows(got, oracle_dir(x, 1), tol32(n), f"register path N={n}")
 
 
@@ -159,14 +159,14 @@ def test_fourstep_forward(lib, lg):
 
 @pytest.mark.parametrize("lg,passes", [(15, 2), (17, 2), (20, 2), (22, 3), (23, 3)])
 @pytest.mark.parametrize("d", ["fwd", "inv"])
-def test_fourstep_register_columns(lib, monkeypatch, lg, passes, d):
+def test_fourstep_register_columns(hooks_lib, monkeypatch, lg, passes, d):
     """The column passes from registers instead of tensor-TMA boxes (the
     default multi-pass plans stage them by TMA)."""
     monkeypatch.setenv("GBFFT_COLTMA", "0")
     monkeypatch.setenv("GBFFT_PASSES", str(passes))
     n = 1 << lg
     x = workloads.cgauss(n, 1, seed=3100 + lg)
-    got = run_1d(lib, x, DIRS[d])
+    got = run_1d(hooks_lib, x, DIRS[d])
     assert_rows(got, oracle_dir(x, DIRS[d]), tol32(n), f"register columns N=2^{lg} {d}")
 
 
@@ -187,32 +187,32 @@ def test_fourstep_in_place(lib):
 
 
 @pytest.mark.parametrize("split", [7, 9, 12])
-def test_fourstep_other_splits(lib, monkeypatch, split):
+def test_fourstep_other_splits(hooks_lib, monkeypatch, split):
     """The same transform through different N1 x N2 splits."""
     monkeypatch.setenv("GBFFT_FORCE_SPLIT", str(split))
     n = 1 << 20
     x = workloads.cgauss(n, 1, seed=5000 + split)
-    got = run_1d(lib, x, 0)
+    got = run_1d(hooks_lib, x, 0)
     assert_rows(got, oracle_dir(x, 0), tol32(n), f"split 2^{split} x 2^{20 - split}")
 
 
 @pytest.mark.parametrize("lg,batch", [(15, 2), (18, 2), (21, 1), (23, 1)])
 @pytest.mark.parametrize("d", ["fwd", "inv"])
-def test_three_pass_split(lib, monkeypatch, lg, batch, d):
+def test_three_pass_split(hooks_lib, monkeypatch, lg, batch, d):
     """N = N1*N2*N3 in three passes (the default from 2^22 up), forced at
     smaller sizes too."""
     monkeypatch.setenv("GBFFT_PASSES", "3")
     n = 1 << lg
     x = workloads.cgauss(n, batch, seed=5500 + lg)
-    got = run_1d(lib, x, DIRS[d])
+    got = run_1d(hooks_lib, x, DIRS[d])
     assert_rows(got, oracle_dir(x, DIRS[d]), tol32(n), f"three-pass {d} N=2^{lg}")
 
 
-def test_two_pass_forced_at_2_24(lib, monkeypatch):
+def test_two_pass_forced_at_2_24(hooks_lib, monkeypatch):
     monkeypatch.setenv("GBFFT_PASSES", "2")
     n = 1 << 24
     x = workloads.uniform(n, 1, seed=5600)
-    got = run_1d(lib, x, 0)
+    got = run_1d(hooks_lib, x, 0)
     assert_rows(got, oracle.fft(x.astype(np.complex128)), tol32(n), "two-pass 2^24")
 
 
@@ -280,21 +280,21 @@ def test_2d(lib, ny, nx, batch, d):
         assert oracle.rel_l2(got[b], ref[b]) <= tol, f"2-D {ny}x{nx} {d}"
 
 
-def test_2d_one_column_pass_forced(lib, monkeypatch):
+def test_2d_one_column_pass_forced(hooks_lib, monkeypatch):
     monkeypatch.setenv("GBFFT_2D_ONE_COLUMN_PASS", "1")
     x = workloads.cgauss(4096 * 32, 2, seed=77).reshape(2, 4096, 32)
-    got = run_2d(lib, x, 0)
+    got = run_2d(hooks_lib, x, 0)
     ref = oracle.fft2(x.astype(np.complex128))
     for b in range(2):
         assert oracle.rel_l2(got[b], ref[b]) <= tol32(4096 * 32)
 
 
 @pytest.mark.parametrize("ny,nx,batch", [(4096, 64, 2), (256, 512, 1), (2048, 16, 3)])
-def test_2d_tensor_tma_columns(lib, monkeypatch, ny, nx, batch):
+def test_2d_tensor_tma_columns(hooks_lib, monkeypatch, ny, nx, batch):
     """Column passes staged by tensor-TMA boxes (opt-in for 2-D plans)."""
     monkeypatch.setenv("GBFFT_COLTMA", "1")
     x = workloads.cgauss(ny * nx, batch, seed=ny + nx + 7).reshape(batch, ny, nx)
-    got = run_2d(lib, x, 1)
+    got = run_2d(hooks_lib, x, 1)
     ref = oracle.fft2(x.astype(np.complex128), oracle.INVERSE)
     for b in range(batch):
         assert oracle.rel_l2(got[b], ref[b]) <= tol32(ny * nx)
@@ -326,3 +326,20 @@ def test_missing_workspace(lib):
     assert lib.fft_plan_set_workspace(h, None) == 0       # library-owned workspace
     assert lib.fft_exec(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), s) == 0
     lib.fft_destroy(h)
+
+
+def test_product_library_ignores_planner_variables(lib, hooks_lib, monkeypatch):
+    """Planner overrides in the environment change plans only in the test
+    build: libgbfft.so builds its default plan whatever the variables say."""
+    monkeypatch.setenv("GBFFT_PASSES", "3")
+    monkeypatch.setenv("GBFFT_FORCE_SPLIT", "9")
+    configs = {}
+    for name, L in (("product", lib), ("test build", hooks_lib)):
+        h = ctypes.c_void_p(L.fft_plan_create(1 << 20, 1, 0, 0))
+        assert h.value
+        c = _lib.FftPlanConfig()
+        assert L.fft_plan_get_config(h, ctypes.byref(c)) == 0
+        configs[name] = (c.npass, c.lg1)
+        L.fft_destroy(h)
+    assert configs["test build"][0] == 3
+    assert configs["product"][0] == 2 and configs["product"][1] != 9

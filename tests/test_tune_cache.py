@@ -21,6 +21,16 @@ def test_shipped_entries_are_well_formed():
     fields = [name for name, _ in _lib.FftPlanConfig._fields_]
     assert shipped
     for k, v in shipped.items():
+        if "|many|" in k:
+            # uneven batch: GPU | many | count=C | lengths=<digest>, an fft_many_config
+            dev, kind, count, digest = k.split("|")
+            assert dev and int(count[6:]) >= 1 and len(digest) == len("lengths=") + 16, k
+            c = v["config"]
+            assert sorted(c) == ["ctas_per_sm", "gap", "lg1"] and 1 <= c["gap"] <= 16 and c["ctas_per_sm"] >= 1, k
+            assert len(c["lg1"]) == 4 and all(7 <= c["lg1"][i] <= 8 and 6 <= 13 + i - c["lg1"][i] <= 8
+                                              for i in range(4)), k
+            assert _lib.FftManyConfig.from_dict(c).as_dict() == c and v["us"] > 0
+            continue
         dev, n, batch, prec = k.split("|")
         n, batch, prec = int(n[2:]), int(batch[6:]), int(prec[5:])
         lg = n.bit_length() - 1
@@ -78,3 +88,14 @@ def test_corrupt_cache_is_replaced(fake_tuner):
     cfg = tune.tuned_config(256, 2, 0, device="cpu")
     assert fake_tuner == [(256, 2, 0)]
     assert _read_json(path) == {"dev|n=256|batch=2|prec=0": {"config": cfg, "us": 2.0}}
+
+
+def test_many_key_is_the_length_list(monkeypatch):
+    """The uneven-batch cache key depends on the GPU model and on the exact
+    length list (order included), not on anything else."""
+    monkeypatch.setattr(tune.torch.cuda, "get_device_name", lambda d=None: "Some GPU")
+    a = tune.many_key([256, 512, 8192], 0)
+    assert a.startswith("Some_GPU|many|count=3|lengths=")
+    assert tune.many_key([256, 512, 8192], 0) == a
+    assert tune.many_key([512, 256, 8192], 0) != a
+    assert tune.many_key([256, 512], 0) != a
