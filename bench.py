@@ -775,6 +775,9 @@ def run_case(args):
     batch = args.batch or max(1, (TOTAL // 2 if fp64 else TOTAL) // n)
     if args.real:
         h = lib.fft_plan_create_r2c(n, batch, args.prec)
+    elif args.tma >= 0:
+        c = _lib.FftPlanConfig.from_dict({"tma": args.tma})
+        h = lib.fft_plan_create_config(n, batch, args.dir, args.prec, ctypes.byref(c))
     else:
         h = lib.fft_plan_create(n, batch, args.dir, args.prec)
     if not h:
@@ -1137,6 +1140,7 @@ def main():
     ap.add_argument("--filter", action="store_true", help="with --case: range compression instead of the FFT")
     ap.add_argument("--case-n", type=int, default=0, help="profiling case of any supported length n")
     ap.add_argument("--real", action="store_true", help="with --case/--case-n: a real-data plan (--dir 0 r2c, 1 c2r)")
+    ap.add_argument("--tma", type=int, default=-1, help="with --case: the configuration's tma field (-1: planner default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

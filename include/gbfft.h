@@ -244,7 +244,9 @@ GBFFT_API int fft_pointer_usable(const void* ptr, size_t bytes);
  * cp.async.bulk of contiguous tiles; multi-pass: column passes staged by
  * tensor TMA boxes), 2 = single pass 2^12..2^14 only: persistent register-path
  * kernel that prefetches the next transform into L2 while computing one,
- * 0 = register path.  fused: 1 = both passes of a two-pass split in one
+ * 3 = as 2, and once the last pass has read the exchange buffer a bulk copy
+ * brings the next transform into it, so the first pass reads shared memory
+ * (inputs not 16-byte aligned take the tma = 2 kernel), 0 = register path.  fused: 1 = both passes of a two-pass split in one
  * persistent launch that pipelines slabs of the batch through an L2-resident
  * workspace (2^13..2^18; split and columns fixed by the kernel), 0 = one launch
  * per pass.  halves: single pass only, 2 = two CTAs per transform, each

@@ -84,6 +84,8 @@ struct fft_plan {
   const gbfft::TileKernelInfo* ktma;  // persistent TMA-staged single-pass kernel (or NULL)
   const gbfft::TileKernelInfo* kdif2; // two-CTA radix-2 split kernel (or NULL)
   const gbfft::TileKernelInfo* kpf;   // persistent L2-prefetching single-pass kernel (or NULL)
+  const gbfft::TileKernelInfo* kpfs;  // its variant staging the next transform by a bulk copy (or NULL;
+                                      // kpf is then the fallback for inputs not 16-byte aligned)
   long long pf_grid;                  // its resident-CTA grid
   const gbfft::TileKernelInfo* krc;   // fused range-compression kernel of the length (or NULL)
   void* d_rctw;                       // its remainder-last stage table (NULL: the length's own table)

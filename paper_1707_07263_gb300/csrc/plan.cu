@@ -282,6 +282,17 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
   a.ncols = p->batch;
   a.conj_in = x.conj;
   set_out_xf(a, x);
+  if (p->kpfs && ((uintptr_t)in & 15) == 0) {
+    // bulk copies need a 16-byte aligned source (rows are L * 8 bytes apart)
+    long long ntiles = a.tiles_per_batch;
+    const long long grid = p->pf_grid < ntiles ? p->pf_grid : ntiles;
+    int* st = p->d_status;
+    void* args[] = {(void*)&a, (void*)&ntiles, (void*)&st};
+    return cudaLaunchKernel(p->kpfs->fn, dim3((unsigned)grid), dim3(p->kpfs->threads), args,
+                            (size_t)p->kpfs->smem_bytes, s) == cudaSuccess
+               ? FFT_OK
+               : FFT_ERR_CUDA;
+  }
   if (p->kpf) {
     long long ntiles = a.tiles_per_batch;
     const long long grid = p->pf_grid < ntiles ? p->pf_grid : ntiles;
@@ -617,18 +628,29 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     // measured on GB300 it pays where one CTA fills an SM (2^14: 279 -> 248
     // us per 2^26 points), not at 2^13 (two CTAs per SM already overlap)
     // nor at 2^12 (its loop costs a resident CTA).
+    // tma = 3 (the default at 2^13 and 2^14): the same loop, with the next
+    // transform brought into the exchange buffer by a bulk copy issued once
+    // the last pass has read it (measured on GB300 per 2^26 points: 2^14 248
+    // -> 242 us, 2^13 241 -> 228 us; no change at 2^12).
     const int env_pf = env_int("GBFFT_PF", -1);
+    const bool dflt_pf = env_pf >= 0 ? env_pf > 0 : (lgN == 13 || lgN == 14);
     const bool want_pf = tile_kernel_pf(lgN) && p->prec == FFT_PREC_FP32 && cfg->halves != 2 &&
-                         (cfg->tma == 2 || (cfg->tma < 0 && (env_pf >= 0 ? env_pf > 0 : lgN == 14)));
+                         (cfg->tma == 2 || cfg->tma == 3 || (cfg->tma < 0 && dflt_pf));
     if (want_pf) {
       p->kpf = tile_kernel_pf(lgN);
       rc = prepare_kernel(p->kpf);
       if (rc) return rc;
+      if (cfg->tma == 3 || (cfg->tma < 0 && (env_pf < 0 || env_pf == 3))) {
+        p->kpfs = tile_kernel_pfs(lgN);
+        rc = prepare_kernel(p->kpfs);
+        if (rc) return rc;
+      }
       int per_sm = 0, sms = 0, dev = 0;
       cudaGetDevice(&dev);
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kpf->fn, p->kpf->threads,
-                                                        (size_t)p->kpf->smem_bytes) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kpfs ? p->kpfs->fn : p->kpf->fn, p->kpf->threads,
+                                                        (size_t)(p->kpfs ? p->kpfs->smem_bytes : p->kpf->smem_bytes)) !=
+              cudaSuccess ||
           per_sm < 1)
         return FFT_ERR_CUDA;
       p->pf_grid = (long long)per_sm * sms;
@@ -1152,7 +1174,7 @@ int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
     out->npass = 1;
     out->lg1 = p->lg;
     out->c1 = p->c1;
-    out->tma = p->ktma ? 1 : (p->kpf ? 2 : 0);
+    out->tma = p->ktma ? 1 : (p->kpfs ? 3 : (p->kpf ? 2 : 0));
     out->halves = p->kdif2 ? 2 : 1;
   } else if (p->kind == KIND_FOURSTEP) {
     out->npass = p->npass ? p->npass : 2;

@@ -36,7 +36,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/gbfft.h"
 #include "fft_common.cuh"
+#include "tma_util.cuh"
 
 namespace gbfft {
 
@@ -225,10 +227,15 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 //        2: first pass reads a TMA-staged box; 4: the first pass's inputs are
 //        already in registers (left there by a POST == 2 transform), no conj_in;
 //        5: first pass builds Z[n] = E[n] + i O[n] of a complex-to-real
-//        transform from X[n] and X[L - n] of rows of L + 1 values (C2R).
+//        transform from X[n] and X[L - n] of rows of L + 1 values (C2R);
+//        6: first pass reads an unpadded copy of the C rows that a bulk copy
+//        left at the start of the exchange buffer `sm` (tile_fft_pfs_kernel).
 //   POST 0: last pass stores to global memory; 2: last pass multiplies output
 //        k by filt[k] and conjugates it, in registers; 3: last pass leaves
-//        output k in shared memory at sidx(k) (natural order).
+//        output k in shared memory at sidx(k) (natural order); 4: as 0, and
+//        once every thread has read its inputs from `sm`, one thread starts
+//        the bulk copy of the next tile's rows (source `gin`, none if NULL)
+//        into `sm`, completing on the mbarrier stored just past the tile.
 //   REV: remainder-last radix schedule (tables from a.tw_rev).  A POST == 2
 //        transform (radix-16 last pass: thread j holds k = j + q*L/16) feeds a
 //        PRE == 4, REV transform (radix-16 first pass: thread j reads n = j +
@@ -273,7 +280,11 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       const long long isn = IN_CF ? a.in_sn : 1;
       const float2* p = (OFFS ? gin + (ok ? a.col_off[cc[i]] : 0) : gin + cc[i] * a.in_sc) + (long long)jj[i] * isn;
       const long long step = (long long)LR * isn;
-      if constexpr (PRE == 5) {
+      if constexpr (PRE == 6) {
+        const float2* sp = sm + cc[i] * L + jj[i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i * R + r] = ok ? sp[r * LR] : make_float2(0.f, 0.f);
+      } else if constexpr (PRE == 5) {
         // complex-to-real: E = (X[n] + conj X[L-n]) / 2,
         // O = (X[n] - conj X[L-n]) W_N^{-n} / 2, Z = E + i O; Im X[0] and
         // Im X[L] do not enter.  Rows hold L + 1 values (in_sc).  All loads
@@ -346,6 +357,15 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
 #pragma unroll
         for (int r = 0; r < R; ++r) v[i * R + r] = sm[cc[i] * LP + sidx<IDX>(jj[i] + r * LR)];
       }
+    }
+  }
+  if constexpr (LAST && POST == 4 && !FIRST) {
+    // every thread holds its last-pass inputs: the buffer now receives the
+    // next tile's rows while this pass computes and stores
+    __syncthreads();
+    if (threadIdx.x == 0 && gin) {
+      fence_proxy_async();   // order the generic-proxy reads above before the async-proxy write
+      tma_load_1d(sm, gin, (uint32_t)(C * L * 8), reinterpret_cast<uint64_t*>(sm + Cfg::SM_TILE));
     }
   }
 
@@ -482,7 +502,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   } else {
     // all reads of this pass (or, for PRE == 4, of the previous transform's
     // last pass) are done
-    if constexpr (!FIRST || PRE == 4) __syncthreads();
+    if constexpr (!FIRST || PRE == 4 || PRE == 6) __syncthreads();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = jj[i];
@@ -594,6 +614,58 @@ __global__ void __launch_bounds__(TileCfg<LG, 1, false, false>::T)
     }
     tile_body<LG, 1, false, false>(a, t, smem);
     __syncthreads();   // the next tile's first exchange overwrites this one's
+  }
+}
+
+// Persistent single pass (C = 1) whose exchange buffer doubles as the staging
+// buffer of the next transform: when the last pass of transform t has read its
+// inputs from shared memory, one thread starts a bulk copy (TMA, evict-first)
+// of transform t + grid into the same buffer, which lands while the last pass
+// computes and stores; transform t + grid's first pass then reads shared
+// memory instead of waiting on global loads.  Transform t + grid is also
+// prefetched into L2 when transform t starts, so that the copy reads L2.
+// Shared memory: the exchange tile plus one mbarrier (8 bytes, 16 reserved).
+// The wait on the barrier is bounded: on expiry the CTA records
+// FFT_ERR_TIMEOUT in `status`, waits once more (bounded) for the copy in
+// flight, and returns.
+template <int LG>
+constexpr int pfs_smem_bytes() { return TileCfg<LG, 1, false, false>::SMEM_BYTES + 16; }
+
+template <int LG>
+__global__ void __launch_bounds__(TileCfg<LG, 1, false, false>::T)
+    tile_fft_pfs_kernel(const TileArgs a, long long ntiles, int* status) {
+  extern __shared__ float2 smem[];
+  using Cfg = TileCfg<LG, 1, false, false>;
+  static_assert(Cfg::NST > 1 && Cfg::SM_TILE >= Cfg::L, "the staged copy must fit the exchange buffer");
+  constexpr int BYTES = Cfg::L * 8;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + Cfg::SM_TILE);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (long long)blockIdx.x < ntiles)
+    tma_load_1d(smem, a.in + (long long)blockIdx.x * a.in_gstride, BYTES, mbar);
+  uint32_t parity = 0;
+  float2 v[Cfg::P];
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long nt = t + gridDim.x;
+    const float2* next = nt < ntiles ? a.in + nt * a.in_gstride : nullptr;
+    if (next) {
+      const char* p = (const char*)next;
+#pragma unroll
+      for (int off = threadIdx.x * 128; off < BYTES; off += Cfg::T * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+    }
+    if (!mbar_wait(mbar, parity)) {
+      if (threadIdx.x == 0) atomicExch(status, FFT_ERR_TIMEOUT);
+      mbar_wait(mbar, parity);   // second bounded wait for the copy in flight
+      return;
+    }
+    parity ^= 1;
+    // (no closing barrier: the next transform starts with the wait on its copy,
+    // which the last pass issued after every thread had read the buffer)
+    tile_stage<LG, 1, false, false, 0, false, 6, 4>(v, smem, a, next, a.out + t * a.out_gstride, t, 0, nullptr);
   }
 }
 

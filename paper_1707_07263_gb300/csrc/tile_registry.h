@@ -39,6 +39,9 @@ const TileKernelInfo* tile_kernel_dif2(int lg);
 // Persistent single-pass kernels with an L2 prefetch of the next transform,
 // lengths 2^12..2^14 (one transform per CTA); signature void(TileArgs, long long).
 const TileKernelInfo* tile_kernel_pf(int lg);
+// Persistent 2^12..2^14 kernels staging the next transform into the exchange
+// buffer by a bulk copy (tile_fft_pfs_kernel); signature void(TileArgs, long long, int* status).
+const TileKernelInfo* tile_kernel_pfs(int lg);
 
 // Fused real-to-complex / complex-to-real kernels for half length 2^lg
 // (N = 2^(lg+1) reals), 2^1..2^14, jj_cols(lg) rows per CTA.

@@ -53,6 +53,8 @@ static std::vector<fft_plan_config> candidates(int lgN) {
     if (lgN >= 12) {
       c.tma = 2;  // persistent register path with an L2 prefetch of the next transform
       v.push_back(c);
+      c.tma = 3;  // ... and a bulk copy of it into the exchange buffer
+      v.push_back(c);
     }
     c.tma = 0;
     c.halves = 2;  // rejected where no split kernel exists

@@ -58,6 +58,9 @@ def run_cfg(lib, x: np.ndarray, cfg: dict) -> np.ndarray:
     (12, {"npass": 1, "tma": 2}),
     (13, {"npass": 1, "tma": 2}),
     (14, {"npass": 1, "tma": 2}),
+    (12, {"npass": 1, "tma": 3}),
+    (13, {"npass": 1, "tma": 3}),
+    (14, {"npass": 1, "tma": 3}),
     (14, {"npass": 1, "tma": 0}),
 ])
 def test_explicit_configs(lib, lg, cfg):
@@ -133,3 +136,41 @@ def test_autotune_returns_a_working_config(lib, lg, batch, tmp_path, monkeypatch
     assert oracle.rel_l2_rows(got, oracle.transform(x.astype(np.complex128))).max() <= 5e-7 * lg
     # the cached answer is reused
     assert tune.tuned_config(n, batch, 0) == cfg
+
+
+@pytest.mark.parametrize("lg", [12, 13, 14])
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_staged_persistent_kernel_loops(lib, lg, d):
+    """tma = 3 (the next transform bulk-copied into the exchange buffer once
+    the last pass has read it): several transforms per CTA (batch well above
+    the resident grid), every direction, each transform against the oracle;
+    an 8-byte-aligned input takes the non-staged kernel and gives the same
+    result."""
+    n = 1 << lg
+    batch = 1100 if lg == 14 else 2100
+    x = workloads.cgauss(n, batch, seed=8600 + lg + 17 * d)
+    c = _lib.FftPlanConfig.from_dict({"npass": 1, "tma": 3})
+    h = ctypes.c_void_p(lib.fft_plan_create_config(n, batch, d, 0, ctypes.byref(c)))
+    assert h.value, _lib.ERRORS.get(lib.fft_last_error())
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    buf = torch.zeros(n * batch + 1, dtype=torch.complex64, device="cuda")
+    xt = buf[:-1]
+    xt.copy_(torch.from_numpy(x.reshape(-1)))
+    assert xt.data_ptr() % 16 == 0
+    out = torch.empty_like(xt)
+    assert lib.fft_exec(h, ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(out.data_ptr()), s) == 0
+    x8 = buf[1:]
+    x8.copy_(torch.from_numpy(x.reshape(-1)))
+    assert x8.data_ptr() % 16 == 8
+    out8 = torch.empty_like(x8)
+    assert lib.fft_exec(h, ctypes.c_void_p(x8.data_ptr()), ctypes.c_void_p(out8.data_ptr()), s) == 0
+    torch.cuda.synchronize()
+    assert lib.fft_status(h, s) == 0
+    lib.fft_destroy(h)
+    x64 = x.astype(np.complex128)
+    ref = {0: oracle.fft(x64), 1: oracle.fft(x64, oracle.INVERSE), 2: oracle.fft(x64, oracle.ADJOINT),
+           3: oracle.fft(x64) / n}[d]
+    got = out.cpu().numpy().reshape(batch, n)
+    assert oracle.rel_l2_rows(got, ref).max() <= 5e-7 * lg
+    got8 = out8.cpu().numpy().reshape(batch, n)
+    assert oracle.rel_l2_rows(got8, ref).max() <= 5e-7 * lg
