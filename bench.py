@@ -67,8 +67,8 @@ def measured_peaks():
 # register, prefetching and TMA-staged kernels and what they include).  The
 # DRAM traffic recorded in profiles/traffic.json is valid only while these
 # files are unchanged.
-BENCH_KERNEL_SOURCES = ("fft_common.cuh", "tile_fft.cuh", "tile_fft_tma.cuh", "tile_registry.h", "tile_inst_jj.cu",
-                        "tile_inst_pf.cu", "tile_inst_tma.cu")
+BENCH_KERNEL_SOURCES = ("fft_common.cuh", "tile_fft.cuh", "tile_fft_tma.cuh", "tma_util.cuh", "tile_registry.h",
+                        "tile_inst_jj.cu", "tile_inst_pf.cu", "tile_inst_tma.cu")
 
 
 def source_hash() -> str:
@@ -88,7 +88,7 @@ def single_kernel_name(lib, h) -> str:
     _lib.check(lib.fft_plan_get_config(h, ctypes.byref(c)))
     if c.halves == 2:
         return "tile_fft_dif2_kernel"
-    return {1: "tile_fft_tma_kernel", 2: "tile_fft_pf_kernel"}.get(c.tma, "tile_fft_kernel")
+    return {1: "tile_fft_tma_kernel", 2: "tile_fft_pf_kernel", 3: "tile_fft_pfs_kernel"}.get(c.tma, "tile_fft_kernel")
 
 
 def ncu_traffic(kernel_key: str):
