@@ -51,6 +51,17 @@ struct MixedArgs {
   double sx, sy;      // output scale (1/N of Eq. 2 exact to FP64 for the FP64 kernel)
   float fsx, fsy;     // the same rounded to FP32 for the FP32 kernel
 };
+// Mixed-radix lengths with a compile-time three-pass schedule (mixed_ct.cu).
+struct MixedCtInfo {
+  long long N;
+  int r0, r1, r2;
+  int C;           // transforms per CTA
+  int threads;     // threads per CTA
+  bool pad;        // padded shared-memory index (msidx)
+  const void* fn;  // kernel void(MixedArgs)
+};
+const MixedCtInfo* mixed_ct_lookup(long long N);
+
 int mixed_radices(long long N, int* rad);
 int mixed_plan_init(fft_plan* p);
 int mixed_exec(fft_plan* p, const void* in, void* out, int conj, double sx, double sy, int scale_out,
@@ -106,6 +117,7 @@ struct fft_plan {
   // mixed-radix plans (KIND_MIXED)
   gbfft::MixedArgs mixed;
   int mixed_threads, mixed_smem, mixed_pad;
+  const gbfft::MixedCtInfo* mixed_ct;   // compile-time schedule for this length (FP32), or NULL
   const float2* pre_tw;               // its W_N^n table, n < N/2
   long long tma_grid;                 // its resident-CTA grid
 

@@ -1,0 +1,280 @@
+// mixed_ct.cu -- mixed-radix transforms (N = 2^a 3^b 5^c) with the radix
+// schedule fixed at compile time for common lengths, in three passes of
+// composite register radices.
+//
+// The run-time kernel (mixed.cu) takes one pass per prime factor or radix-16
+// block: N = 1000 = 8*5*5*5 costs four passes, 12000 seven, each a round trip
+// through shared memory plus run-time index divisions.  Sec. 2.1's split
+// holds for any factorisation, so here N = R0 * R1 * R2 with composite
+// radices of 10..25 points kept in registers (a radix R = A * B is itself a
+// Cooley-Tukey split: A-point DFTs, the inner twiddles W_R^{n2 k1} as
+// compile-time constants, B-point DFTs).  Every length below takes three
+// passes, two exchanges through shared memory; N, the radices and every
+// divisor are template parameters, so the index arithmetic folds to
+// multiplications and shifts.
+//
+// Passes follow the same Stockham recurrence as mixed.cu (natural order in
+// and out): butterfly j of a pass with radix R and Ns = the product of the
+// earlier radices reads a[j + r N/R], multiplies by W_{Ns R}^{r (j mod Ns)}
+// (powers of one W_N table entry), runs the R-point DFT and writes
+// b[(j div Ns) Ns R + (j mod Ns) + q Ns].  FP32 only; other lengths, and
+// FP64, take the run-time kernel.
+#include <cuda_runtime.h>
+
+#include <utility>
+
+#include "gbfft_internal.h"
+#include "mixed_common.cuh"
+
+namespace gbfft {
+
+// ---- compile-time cos / sin of 2 pi m / R --------------------------------
+// (Taylor series on |x| <= pi/4 after reduction by the octant symmetries of
+// the unit circle; double precision, rounded once to FP32 where used)
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+
+constexpr double ct_sin_poly(double x) {   // |x| <= pi/4
+  double term = x, sum = x;
+  for (int k = 1; k < 12; ++k) {
+    term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double ct_cos_poly(double x) {   // |x| <= pi/4
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 12; ++k) {
+    term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    sum += term;
+  }
+  return sum;
+}
+// cos and sin of 2 pi m / R: the angle in eighths of a turn, e = 8m / R,
+// splits into an octant o = floor(e) and a remainder; each octant maps to a
+// first-octant angle by an exact rotation or reflection.
+constexpr void ct_cossin(int m, int R, double& c, double& s) {
+  m %= R;
+  if (m < 0) m += R;
+  const int o = (8 * m) / R;                          // octant 0..7
+  const double frac = (double)(8 * m - o * R) / R;    // in [0, 1)
+  double t = frac * kPiD / 4.0;                        // angle within the octant
+  double cc = 0, ss = 0;
+  // odd octants measure the angle from the next multiple of pi/4 downwards
+  if (o & 1) t = kPiD / 4.0 - t;
+  const double ct = ct_cos_poly(t), st = ct_sin_poly(t);
+  switch (o) {
+    case 0: cc = ct; ss = st; break;     // [0, pi/4)
+    case 1: cc = st; ss = ct; break;     // [pi/4, pi/2): pi/2 - t
+    case 2: cc = -st; ss = ct; break;    // [pi/2, 3pi/4): pi/2 + t
+    case 3: cc = -ct; ss = st; break;    // [3pi/4, pi): pi - t
+    case 4: cc = -ct; ss = -st; break;   // [pi, 5pi/4): pi + t
+    case 5: cc = -st; ss = -ct; break;   // [5pi/4, 3pi/2): 3pi/2 - t
+    case 6: cc = st; ss = -ct; break;    // [3pi/2, 7pi/4): 3pi/2 + t
+    default: cc = ct; ss = -st; break;   // [7pi/4, 2pi): 2pi - t
+  }
+  c = cc;
+  s = ss;
+}
+constexpr double ct_cos(int m, int R) {
+  double c = 0, s = 0;
+  ct_cossin(m, R, c, s);
+  return c;
+}
+constexpr double ct_sin(int m, int R) {
+  double c = 0, s = 0;
+  ct_cossin(m, R, c, s);
+  return s;
+}
+
+// a * W_R^M (W_R = exp(-2 pi i / R)) for compile-time R, M: quarter turns are
+// exact rotations, eighth turns two products, the rest a complex product with
+// constant factors.
+template <int R, int M>
+__device__ __forceinline__ float2 mul_wc(float2 a) {
+  constexpr int m = M % R;
+  if constexpr (m == 0) {
+    return a;
+  } else if constexpr ((4 * m) % R == 0) {
+    constexpr int qt = 4 * m / R;   // W^m = (-i)^qt
+    if constexpr (qt == 1) return make_float2(a.y, -a.x);
+    else if constexpr (qt == 2) return make_float2(-a.x, -a.y);
+    else return make_float2(-a.y, a.x);
+  } else if constexpr ((8 * m) % R == 0) {
+    constexpr int et = 8 * m / R;   // odd eighth of a turn
+    if constexpr (et == 1) return make_float2(GBFFT_R2 * (a.x + a.y), GBFFT_R2 * (a.y - a.x));
+    else if constexpr (et == 3) return make_float2(GBFFT_R2 * (a.y - a.x), -GBFFT_R2 * (a.x + a.y));
+    else if constexpr (et == 5) return make_float2(-GBFFT_R2 * (a.x + a.y), GBFFT_R2 * (a.x - a.y));
+    else return make_float2(GBFFT_R2 * (a.x - a.y), GBFFT_R2 * (a.x + a.y));
+  } else {
+    constexpr float c = (float)ct_cos(m, R), s = (float)ct_sin(m, R);
+    return cmul(a, make_float2(c, -s));
+  }
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = B..E-1
+template <int B, int E, typename F>
+__device__ __forceinline__ void ct_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    ct_for<B + 1, E>(f);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void ct_dft(float2* v);
+
+// R = A * B, n = B n1 + n2, k = k1 + A k2:
+//   X[k1 + A k2] = sum_{n2} W_B^{n2 k2} W_R^{n2 k1} sum_{n1} x[B n1 + n2] W_A^{n1 k1}
+template <int A, int B>
+__device__ __forceinline__ void ct_dft_split(float2* v) {
+  constexpr int R = A * B;
+  float2 x[B][A];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2)
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) x[n2][n1] = v[B * n1 + n2];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) ct_dft<A>(x[n2]);
+  ct_for<1, B>([&](auto n2c) {
+    constexpr int n2 = decltype(n2c)::value;
+    ct_for<1, A>([&](auto k1c) {
+      constexpr int k1 = decltype(k1c)::value;
+      x[n2][k1] = mul_wc<R, n2 * k1>(x[n2][k1]);
+    });
+  });
+  float2 y[A][B];
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1)
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) y[k1][n2] = x[n2][k1];
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) ct_dft<B>(y[k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = y[k1][k2];
+}
+
+template <int R>
+__device__ __forceinline__ void ct_dft(float2* v) {
+  if constexpr (R == 2 || R == 4 || R == 8 || R == 16) dft_fwd<R>(v);
+  else if constexpr (R == 3 || R == 5 || R == 7) dft_odd<R>(v);
+  else if constexpr (R == 10) ct_dft_split<2, 5>(v);
+  else if constexpr (R == 12) ct_dft_split<4, 3>(v);
+  else if constexpr (R == 15) ct_dft_split<3, 5>(v);
+  else if constexpr (R == 20) ct_dft_split<4, 5>(v);
+  else if constexpr (R == 24) ct_dft_split<8, 3>(v);
+  else {
+    static_assert(R == 25, "compiled radices: 2, 3, 4, 5, 7, 8, 10, 12, 15, 16, 20, 24, 25");
+    ct_dft_split<5, 5>(v);
+  }
+}
+
+// largest power of two <= r (r >= 1)
+constexpr int ct_hp2(int r) { return r >= 16 ? 16 : r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1; }
+
+// v[r] *= w^r, r = 1..R-1, w = W_N^e: the powers w^{2^i} < R are loaded from
+// the W_N table (r e < N for every r < R, so no reduction is needed), the
+// others are products of one loaded power and an earlier power.
+template <int R>
+__device__ __forceinline__ void ct_twiddles(float2* v, const float2* tw, int e) {
+  float2 w[R];
+#pragma unroll
+  for (int p = 1; p < R; p *= 2) w[p] = __ldg(tw + p * e);
+  ct_for<3, R>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    constexpr int h = ct_hp2(r);
+    if constexpr (h != r) w[r] = cmul(w[h], w[r - h]);
+  });
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+}
+
+// One pass over the tile's C transforms: radix R, Ns = NS.
+template <int N, int R, int NS, bool PAD, bool FIRST, bool LAST>
+__device__ __forceinline__ void ct_pass(const MixedArgs& a, const float2* src, float2* dst, long long col0) {
+  constexpr int NB = N / R;
+  constexpr int STRIDE = N / (NS * R);
+  static_assert(N % (NS * R) == 0, "schedule");
+  const float2* tw = (const float2*)a.tw;
+  const int total = a.C * NB;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int c = b / NB, j = b - c * NB;
+    const bool ok = col0 + c < a.batch;
+    float2 v[R];
+    const int n0 = c * N + j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (FIRST)
+        v[r] = ok ? __ldcs(src + n0 + r * NB) : make_float2(0.f, 0.f);
+      else
+        v[r] = src[msidx<PAD>(n0 + r * NB)];
+    }
+    if (FIRST && a.conj_in) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
+    }
+    const int jq = j / NS, k = j - jq * NS;
+    if constexpr (NS > 1) ct_twiddles<R>(v, tw, k * STRIDE);
+    ct_dft<R>(v);
+    const int m0 = c * N + jq * NS * R + k;
+    if constexpr (LAST) {
+      if (!ok) continue;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        float2 y = v[q];
+        if (a.scale_out) y = make_float2(y.x * a.fsx, y.y * a.fsy);
+        __stcs(dst + m0 + q * NS, y);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) dst[msidx<PAD>(m0 + q * NS)] = v[q];
+    }
+  }
+}
+
+// The tile of C transforms: three passes R0, R1, R2 (in == out is safe: the
+// first pass reads the whole tile into shared memory before the last writes).
+template <int N, int R0, int R1, int R2, bool PAD, int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) mixed_ct_kernel(const MixedArgs a) {
+  static_assert(R0 * R1 * R2 == N, "schedule");
+  extern __shared__ __align__(16) unsigned char ct_smem[];
+  float2* const buf0 = (float2*)ct_smem;
+  float2* const buf1 = buf0 + msidx<PAD>(a.C * N - 1) + 1;
+  const long long col0 = (long long)blockIdx.x * a.C;
+  const float2* in = (const float2*)a.in + col0 * N;
+  float2* out = (float2*)a.out + col0 * N;
+  ct_pass<N, R0, 1, PAD, true, false>(a, in, buf0, col0);
+  __syncthreads();
+  ct_pass<N, R1, R0, PAD, false, false>(a, buf0, buf1, col0);
+  __syncthreads();
+  ct_pass<N, R2, R0 * R1, PAD, false, true>(a, buf1, out, col0);
+}
+
+// Compiled schedules, each the fastest of the orders and factorisations
+// measured on GB300 for its length (radix 25 first, then 8 or 16; e.g.
+// N = 1000: [25, 8, 5] 203 us against 312 for [10, 10, 10] and 420 for the
+// run-time kernel's [8, 5, 5, 5], per 2^26 points), the transforms per CTA,
+// C = floor(4096 / N) as for the run-time kernel, and the threads per CTA
+// (512 where one CTA fills an SM's shared memory, 8000 and up: 12000 350 -> 324
+// us; 256 below, where two or three CTAs share an SM).
+// (Tiles chosen instead to spread every pass's butterflies evenly over the
+// threads -- N = 1000: 5 transforms, 3000: 2 -- measured slower: the larger
+// tiles cost resident CTAs.)  The padded layout where the first pass writes at
+// an even stride.
+#define GBFFT_CT(N, R0, R1, R2, C, T) \
+  {N, R0, R1, R2, C, T, (R0 % 2 == 0), (const void*)&mixed_ct_kernel<N, R0, R1, R2, (R0 % 2 == 0), T>}
+
+const MixedCtInfo* mixed_ct_lookup(long long N) {
+  static const MixedCtInfo tab[] = {
+      GBFFT_CT(1000, 25, 8, 5, 4, 256),    GBFFT_CT(1200, 25, 16, 3, 3, 256),   GBFFT_CT(1500, 25, 12, 5, 2, 256),
+      GBFFT_CT(2000, 25, 16, 5, 2, 256),   GBFFT_CT(2400, 25, 8, 12, 1, 256),   GBFFT_CT(3000, 25, 8, 15, 1, 256),
+      GBFFT_CT(4000, 25, 16, 10, 1, 256),  GBFFT_CT(5000, 25, 8, 25, 1, 256),   GBFFT_CT(6000, 25, 16, 15, 1, 256),
+      GBFFT_CT(8000, 25, 16, 20, 1, 512),  GBFFT_CT(10000, 25, 16, 25, 1, 512), GBFFT_CT(12000, 25, 24, 20, 1, 512),
+  };
+  for (const MixedCtInfo& t : tab)
+    if (t.N == N) return &t;
+  return nullptr;
+}
+
+}  // namespace gbfft

@@ -21,7 +21,8 @@ from paper_1707_07263_gb300 import workloads
 pytestmark = pytest.mark.gpu
 
 LENGTHS = [3, 5, 6, 7, 9, 10, 12, 14, 15, 21, 24, 25, 27, 35, 48, 49, 60, 80, 96, 100, 105, 120, 125, 243,
-           343, 360, 384, 500, 625, 720, 1000, 1080, 1536, 2000, 2187, 2401, 3000, 3072, 4000, 4800, 5000,
+           343, 360, 384, 500, 625, 720, 1000, 1080, 1200, 1500, 1536, 2000, 2187, 2400, 2401, 3000, 3072, 4000,
+           4800, 5000,
            6000, 7000, 8000, 9000, 10000, 12000, 12288, 14000, 14336]
 
 
@@ -98,3 +99,24 @@ def test_round_trip_and_gradient_through_the_api():
     x64, w64 = x.astype(np.complex128), w.astype(np.float64)
     g_ref = np.stack([2 * oracle.transform(w64 ** 2 * oracle.transform(r), oracle.ADJOINT) for r in x64])
     assert oracle.rel_l2(xt.grad.cpu().numpy(), g_ref) <= 2 * tol(n)
+
+
+# lengths with a compile-time three-pass schedule of composite radices
+# (10, 12, 15, 20, 24, 25 points in registers)
+COMPILED = [1000, 1200, 1500, 2000, 2400, 3000, 4000, 5000, 6000, 8000, 10000, 12000]
+
+
+@pytest.mark.parametrize("n", COMPILED)
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_compiled_schedules(n, d):
+    """Every compiled length, every direction, with a batch that leaves the
+    last tile partly filled (tiles hold floor(4096 / N) transforms), and in
+    place for the forward direction."""
+    c = max(1, 4096 // n)
+    batch = 3 * c + 1 if c > 1 else 5
+    x = workloads.cgauss(n, batch, seed=7700 + n + d)
+    got = run(x, d)
+    assert oracle.rel_l2_rows(got, ref(x, d)).max() <= tol(n), f"N={n} dir={d}"
+    if d == 0:
+        got_ip = run(x, 0, inplace=True)
+        assert np.array_equal(got_ip, got), f"in place N={n}"
