@@ -12,6 +12,8 @@
    n the kernel can meet (d, n < 2^14 + 1024)."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
@@ -52,3 +54,33 @@ def test_reciprocal_division_is_exact():
         m = np.uint64(((1 << 32) + d - 1) // d)
         q = (n * m) >> np.uint64(32)
         assert np.array_equal(q, n // np.uint64(d)), d
+
+
+def test_compile_time_twiddle_constants(tmp_path):
+    """The compile-time cos / sin of 2 pi m / R that the compiled mixed-radix
+    schedules use as inner twiddles (csrc/ct_trig.h, a Taylor series after
+    octant reduction) agree with the host math library to 1e-15 for every
+    m < R of every composite radix and a range of other R."""
+    import math
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "t.cpp"
+    src.write_text('#include <cstdio>\n#include "ct_trig.h"\n'
+                   'int main() { for (int R = 1; R <= 64; ++R) for (int m = -R; m < 2 * R; ++m) '
+                   'printf("%d %d %.17g %.17g\\n", m, R, gbfft::ct_cos(m, R), gbfft::ct_sin(m, R)); return 0; }\n')
+    exe = tmp_path / "t"
+    subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", os.path.join(root, "paper_1707_07263_gb300", "csrc"),
+                           str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    worst = 0.0
+    count = 0
+    for line in out:
+        if not line:
+            continue
+        m, r, c, s = line.split()
+        m, r = int(m), int(r)
+        ang = 2.0 * math.pi * (m % r) / r
+        worst = max(worst, abs(float(c) - math.cos(ang)), abs(float(s) - math.sin(ang)))
+        count += 1
+    assert count == sum(3 * r for r in range(1, 65))
+    assert worst <= 1e-15, worst
