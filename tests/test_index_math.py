@@ -59,10 +59,12 @@ def test_reciprocal_division_is_exact():
 def test_compile_time_twiddle_constants(tmp_path):
     """The compile-time cos / sin of 2 pi m / R that the compiled mixed-radix
     schedules use as inner twiddles (csrc/ct_trig.h, a Taylor series after
-    octant reduction) agree with the host math library to 1e-15 for every
-    m < R of every composite radix and a range of other R."""
-    import math
+    octant reduction) agree with a 30-digit evaluation (mpmath) to 4e-16
+    (two units in the last place at magnitude 1) for every m of R = 1..64,
+    including negative m and m >= R."""
     import subprocess
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     src = tmp_path / "t.cpp"
     src.write_text('#include <cstdio>\n#include "ct_trig.h"\n'
@@ -79,8 +81,8 @@ def test_compile_time_twiddle_constants(tmp_path):
             continue
         m, r, c, s = line.split()
         m, r = int(m), int(r)
-        ang = 2.0 * math.pi * (m % r) / r
-        worst = max(worst, abs(float(c) - math.cos(ang)), abs(float(s) - math.sin(ang)))
+        ang = 2 * mpmath.pi * mpmath.mpf(m % r) / r
+        worst = max(worst, abs(float(c) - float(mpmath.cos(ang))), abs(float(s) - float(mpmath.sin(ang))))
         count += 1
     assert count == sum(3 * r for r in range(1, 65))
-    assert worst <= 1e-15, worst
+    assert worst <= 4e-16, worst
