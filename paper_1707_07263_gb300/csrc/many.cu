@@ -187,6 +187,14 @@ __device__ __forceinline__ void many_row_tile(const ManyArgs& m, const ManyItem&
   a.sx = sc;
   a.sy = m.conj ? -sc : sc;
   tile_body<LG2, C, false, true>(a, it.g, smem);
+  // The tile's C rows of the intermediate (C * N2 = 4096 points, 32 KB,
+  // contiguous) have been read by every thread: tile_body's first exchange
+  // barrier follows all its loads.  Nothing reads them again in this
+  // execution, so drop the lines from L2 instead of letting them be written
+  // back to DRAM later (measured before: 838 MB written for 466 MB of output).
+  static_assert(C * (1 << LG2) * 8 == kManyThreads * 128, "one 128-byte line per thread");
+  const char* rows = (const char*)(m.ws + t.ws_off + (long long)it.g * C * N2);
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(rows + threadIdx.x * 128) : "memory");
 }
 
 __global__ void __launch_bounds__(kManyThreads, 4) many_kernel(const ManyArgs m) {
