@@ -71,6 +71,14 @@ cudaError_t launch_gen_twiddles_n64(double2* tab, long long N, long long count, 
 
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false);
 cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);
+// Real-to-complex transforms of N = 2M reals, M a two-pass four-step length
+// with rows of 2^6..2^10 points: the even/odd split folded into the row pass
+// (real_fold.cu).
+struct TileKernelInfo;
+const TileKernelInfo* r2c_fold_kernel_info(int lg2);
+int r2c_fold_launch(const TileKernelInfo* k, const TileArgs& a, long long M, int N1, long long batch,
+                    const float2* r_lo, const float2* r_hi, int r_s, int scale, float s_int, float s_end,
+                    cudaStream_t s);
 cudaError_t launch_r2c_split(const float2* z, float2* x, long long M, long long batch, const float2* lo,
                              const float2* hi, int s, float s_int, float s_end, cudaStream_t st);
 cudaError_t launch_c2r_split(const float2* x, float2* z, long long M, long long batch, const float2* lo,
@@ -107,6 +115,7 @@ struct fft_plan {
   // through `zbuf` (batch*M complex values after the inner workspace)
   const gbfft::TileKernelInfo* kr2c;
   const gbfft::TileKernelInfo* kc2r;
+  const gbfft::TileKernelInfo* krfold;   // real-to-complex: split folded into the inner row pass (or NULL)
   fft_plan* inner;
   void* d_rtw;        // W_N^k, k < M, two-level: r_lo[k & (2^r_s - 1)] * r_hi[k >> r_s]
   const float2* r_lo;

@@ -484,6 +484,25 @@ static int exec_real(fft_plan* p, const float2* in, float2* out, int dir, cudaSt
     return launch_tile(k, a, a.tiles_per_batch, s);
   }
   if (!p->inner || !p->zbuf) return FFT_ERR_NO_WORKSPACE;
+  if (to_complex && p->krfold) {
+    // column pass of the inner plan into its workspace, then the row pass with
+    // the split folded in (rows k1 and N1 - k1 in one tile)
+    const fft_plan* q = p->inner;
+    if (!q->ws) return FFT_ERR_NO_WORKSPACE;
+    const PassDesc& A = q->pass[0];
+    TileArgs a = A.a;
+    a.in = in;
+    a.out = (float2*)q->ws;
+    const int rc = (A.kcol && coltma_usable(A.kcol, a, a.in))
+                       ? coltma_launch(A.kcol, a, A.ntiles, A.col_grid, q->d_status, s)
+                       : launch_tile(A.k, a, A.ntiles, s);
+    if (rc) return rc;
+    TileArgs b = q->pass[1].a;
+    b.in = (const float2*)q->ws;
+    b.out = out;
+    return r2c_fold_launch(p->krfold, b, M, 1 << q->lg1, p->batch, p->r_lo, p->r_hi, p->r_s, adj ? 1 : 0, s_int,
+                           s_end, s);
+  }
   if (to_complex) {
     const int rc = exec_plan(p->inner, in, p->zbuf, FFT_FORWARD, s);
     if (rc) return rc;
@@ -1125,6 +1144,16 @@ static int plan_real(fft_plan* p, int lgN) {
   p->inner = create_1d(M, p->batch, FFT_FORWARD, FFT_PREC_FP32, nullptr);
   if (!p->inner) return fft_last_error();
   p->launches = p->inner->launches + 1;
+  // Two-pass inner plans with rows of 2^6..2^10 points and at least 16 rows:
+  // the real-to-complex split runs inside the row pass (real_fold.cu), two
+  // passes over memory instead of three.
+  const fft_plan* q = p->inner;
+  if (q->kind == KIND_FOURSTEP && q->npass == 2 && !q->fused && q->pass[1].k && q->pass[1].k->map == MAP_JC &&
+      q->lg1 >= 4 && r2c_fold_kernel_info(q->lg2)) {
+    p->krfold = r2c_fold_kernel_info(q->lg2);
+    const int rc = prepare_kernel(p->krfold);
+    if (rc) return rc;
+  }
   p->lg2 = p->inner->lg2;
   p->d_status = p->inner->d_status;
   p->ws_bytes = align256(p->inner->ws_bytes) + (size_t)M * (size_t)p->batch * 8;

@@ -232,7 +232,11 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 //        left at the start of the exchange buffer `sm` (tile_fft_pfs_kernel).
 //   POST 0: last pass stores to global memory; 2: last pass multiplies output
 //        k by filt[k] and conjugates it, in registers; 3: last pass leaves
-//        output k in shared memory at sidx(k) (natural order); 4: as 0, and
+//        output k in shared memory at sidx(k) (natural order) and splits the
+//        real-to-complex pairs of the same row; 6: last pass leaves output k
+//        of column c in shared memory at k * (C + 1) + c (transposed: lanes of
+//        consecutive k write, and lanes of consecutive c read, without bank
+//        conflicts) and stops there (the caller combines rows); 4: as 0, and
 //        once every thread has read its inputs from `sm`, one thread starts
 //        the bulk copy of the next tile's rows (source `gin`, none if NULL)
 //        into `sm`, completing on the mbarrier stored just past the tile.
@@ -298,12 +302,9 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
           w[r] = __ldg(a.r_w + jj[i] + r * LR);
         }
         if (jj[i] == 0) {   // n == 0 only for r == 0
-          x1[0].y = 0.f;
-          x2[0].y = 0.f;
-          if (a.r_end2) {
-            x1[0].x *= 2.f;
-            x2[0].x *= 2.f;
-          }
+          const float em = (float)(1 + a.r_end2);   // 2 for the adjoint of real-to-complex
+          x1[0] = make_float2(x1[0].x * em, 0.f);
+          x2[0] = make_float2(x2[0].x * em, 0.f);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -381,7 +382,15 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   for (int i = 0; i < NB; ++i) dft_fwd<R>(v + i * R);
 
   // ---- scatter outputs ----
-  if constexpr (LAST && POST == 3) {
+  if constexpr (LAST && POST == 6) {
+    static_assert(NB == 1 && IDX == 0 && !OUT_CF && !REV, "rows left in shared memory: contiguous rows");
+    static_assert(L * (C + 1) <= C * LP, "transposed rows fit the exchange buffer");
+    __syncthreads();   // all reads of this pass are done
+    float2* wp = sm + jj[0] * (C + 1) + cc[0];
+#pragma unroll
+    for (int q = 0; q < R; ++q) wp[q * NS * (C + 1)] = v[q];
+    __syncthreads();
+  } else if constexpr (LAST && POST == 3) {
     // real-to-complex split: thread j holds Z[k], k = j + q*NS; the partner
     // Z[L - k] of every one of them lives in thread NS - j (q' = R - 1 - q),
     // or in thread 0 itself for j = 0, so one exchange gives each thread all
