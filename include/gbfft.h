@@ -62,9 +62,12 @@ enum {
   FFT_PREC_TC_FP16 = 2,
   FFT_PREC_TC_BF16_SPLIT = 3,
   FFT_PREC_TC_FP16_SPLIT = 4,
-  /* complex128 data and FP64 arithmetic; 1-D plans of length 2 <= n <= 7168
-   * with n = 2^a 3^b 5^c 7^d (powers of two up to 4096 included), one on-chip
-   * pass; in and out 16-byte aligned */
+  /* complex128 data and FP64 arithmetic; 1-D plans of 7-smooth length
+   * n = 2^a 3^b 5^c 7^d (powers of two included): one on-chip pass for
+   * 2 <= n <= 7168, two strided passes (four-step, workspace) for
+   * 7168 < n <= 7168^2 when n = N1 N2 with N1, N2 <= 7168 (powers of two up
+   * to 2^24); 2-D plans of 7-smooth sides up to 7168; in and out 16-byte
+   * aligned */
   FFT_PREC_FP64 = 5
 };
 
@@ -84,10 +87,16 @@ enum {
 #define FFT_MAX_LOG2_SIDE 14
 
 /* Plan for `batch` 1-D transforms of length n: a power of two, 2 <= n <= 2^28,
- * or (FP32 only) a product n = 2^a 3^b 5^c 7^d with 3 <= n <= 14336 (mixed
- * radix: Eq. 1 holds for any n and the Cooley-Tukey split of Sec. 2.1 for
- * any factorisation; one on-chip pass of radix-16/8/4/2/3/5/7 stages; a
- * config must be NULL).
+ * or (FP32 and FP64) a product n = 2^a 3^b 5^c 7^d (mixed radix: Eq. 1 holds
+ * for any n and the Cooley-Tukey split of Sec. 2.1 for any factorisation;
+ * a config must be NULL).  Mixed-radix lengths up to 14336 run as one on-chip
+ * pass of radix-16/8/4/2/3/5/7 stages; longer ones, up to 14336^2, as the
+ * four-step split n = N1 N2 (N1 the largest divisor of n at most sqrt(n)
+ * whose cofactor N2 is at most 14336): a strided column pass with the twiddle
+ * W_n^{n2 k1}, then a row pass, through a workspace (fft_plan_kind 6).  A
+ * 7-smooth n with no such split, or beyond 14336^2, gives FFT_ERR_UNSUPPORTED.
+ * FP64 plans take the same routes with 7168 in place of 14336, for powers of
+ * two as well (see FFT_PREC_FP64).
  * dir is the direction fft_exec uses (FFT_FORWARD, FFT_INVERSE, optionally
  * with FFT_ADJOINT); prec one of FFT_PREC_*.  Lengths up to 2^14 run as one
  * on-chip pass per transform (Sec. 2.3.2: short data is not partitioned);
@@ -99,9 +108,16 @@ enum {
  * once to FP32; Sec. 2.3.1 look-up table).  Returns NULL on error. */
 GBFFT_API fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec);
 
-/* Plan for `batch` 2-D transforms of ny-by-nx row-major images (powers of two,
- * 2 <= ny, nx <= 2^14): 1-D transforms of every row, then of every column
- * (Sec. 2.3.2: rows, then columns). */
+/* Plan for `batch` 2-D transforms of ny-by-nx row-major images: 1-D
+ * transforms of every row, then of every column (Sec. 2.3.2: rows, then
+ * columns).  Power-of-two sides 2 <= ny, nx <= 2^14 run on the radix-16 tile
+ * kernels (every precision but FP64).  Sides that are 7-smooth but not both
+ * powers of two (FP32, up to 14336), and every FP64 plan (7-smooth sides up
+ * to 7168), run as a row pass and a column pass of the strided mixed-radix
+ * kernel, the column pass in place in the output (no workspace; fft_plan_kind
+ * 6).  A side with a prime factor above 7, or below 2, is FFT_ERR_INVALID_ARG;
+ * a valid side beyond those limits, or tensor-core precisions with a side
+ * that is not a power of two, FFT_ERR_UNSUPPORTED. */
 GBFFT_API fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int prec);
 
 /* Plan for `batch` real-data transforms of length n (power of two,
@@ -303,7 +319,8 @@ GBFFT_API int64_t fft_plan_batch(const fft_plan* plan);
  * of the directions; the folded real-to-complex direction issues one fewer). */
 GBFFT_API int fft_plan_launches(const fft_plan* plan);
 /* Kind: 0 single on-chip pass, 1 four-step, 2 two-dimensional, 3 uneven batch,
- * 4 real data, 5 mixed radix. */
+ * 4 real data, 5 mixed radix (one pass), 6 two strided mixed-radix passes
+ * (mixed-radix or FP64 four-step, mixed-radix or FP64 2-D). */
 GBFFT_API int fft_plan_kind(const fft_plan* plan);
 /* Human-readable plan summary into buf (NUL-terminated); returns FFT_OK. */
 GBFFT_API int fft_plan_describe(const fft_plan* plan, char* buf, size_t len);

@@ -12,9 +12,12 @@ Functions (all FP64, numpy ``complex128`` in and out):
                            summed term by term, O(N^2), over the last axis.
 * ``fft(x, dir)``       -- recursive radix-2 decimation in time (the butterfly
                            of Sec. 2.1), over the last axis.
+* ``dft_bins(x, ks, dir)`` -- the same sum as ``dft`` at the outputs ks only
+                           (O(N) each), for transforms too long for ``dft``.
 * ``fft2(x, dir)``      -- 2-D transform of the last two axes, rows then
                            columns (Sec. 2.3.2 treats the data as 2-D/3-D and
-                           transforms each dimension in turn).
+                           transforms each dimension in turn); sides that are
+                           not powers of two go through ``transform``.
 * ``range_compress(x, H)`` -- SAR range compression by fast convolution, the
   FFT-based SAR processing that Sec. 3 and Sec. 4 name as the method's
   application: every row becomes Eq. 2 applied to H * (Eq. 1 applied to the
@@ -81,6 +84,8 @@ def load_library(path: str | None = None):
         fn.restype = ci
     lib.oracle_fft2.argtypes = [i64, i64, vp, vp, ci]
     lib.oracle_fft2.restype = ci
+    lib.oracle_dft_bins.argtypes = [i64, vp, i64, vp, vp, ci]
+    lib.oracle_dft_bins.restype = ci
     if path is None:
         _lib = lib
     return lib
@@ -119,11 +124,35 @@ def fft(x, dir: int = FORWARD, lib=None) -> np.ndarray:
     return _run_batch("oracle_fft_batch", x, dir, lib)
 
 
+def dft_bins(x, ks, dir: int = FORWARD, lib=None) -> np.ndarray:
+    """Eq. 1 / Eq. 2 / the adjoint of every row of x (last axis) at the outputs
+    ks only: result[..., i] = X[..., ks[i]], each a term-by-term sum."""
+    lib = lib or load_library()
+    a = _prep(x)
+    n = a.shape[-1]
+    k = np.ascontiguousarray(np.asarray(ks, dtype=np.int64).reshape(-1))
+    rows = a.reshape(-1, n)
+    out = np.empty((rows.shape[0], k.size), dtype=np.complex128)
+    for i in range(rows.shape[0]):
+        dst = np.empty(k.size, dtype=np.complex128)
+        rc = lib.oracle_dft_bins(n, _ptr(rows[i]), k.size, k.ctypes.data, _ptr(dst), dir)
+        if rc != 0:
+            raise ValueError(f"oracle_dft_bins: rejected n={n}, dir={dir} (rc={rc})")
+        out[i] = dst
+    return out.reshape(a.shape[:-1] + (k.size,))
+
+
 def fft2(x, dir: int = FORWARD, lib=None) -> np.ndarray:
-    """2-D transform over the last two axes: rows, then columns."""
+    """2-D transform over the last two axes: rows, then columns.  Power-of-two
+    sides run in the C routine; other sides take ``transform`` over the rows
+    and then over the columns (the same definition, any 7-smooth side)."""
     lib = lib or load_library()
     a = _prep(x)
     ny, nx = a.shape[-2], a.shape[-1]
+    if (ny & (ny - 1)) or (nx & (nx - 1)):
+        rows = transform(a, dir, lib)
+        cols = transform(np.swapaxes(rows, -1, -2), dir, lib)
+        return np.ascontiguousarray(np.swapaxes(cols, -1, -2))
     out = np.empty_like(a)
     flat_in = a.reshape(-1, ny, nx)
     flat_out = out.reshape(-1, ny, nx)

@@ -20,10 +20,11 @@
  * Layout: complex values are interleaved (re, im) doubles; a batch of B
  * transforms of length N is B*N complex values, transform b at offset b*N.
  *
- * Two routines:
+ * Routines:
  *   oracle_dft  -- Eq. 1/2 summed term by term, O(N^2).  The exponent n*k is
  *                  reduced mod N first (Eq. 3, periodicity), so every angle is
  *                  2*pi*m/N with 0 <= m < N.
+ *   oracle_dft_bins -- the same sum at chosen outputs k only, O(N) each.
  *   oracle_fft  -- the textbook recursive radix-2 decimation-in-time
  *                  Cooley-Tukey split (the butterfly of Sec. 2.1): even and
  *                  odd samples are transformed separately and combined as
@@ -74,6 +75,32 @@ int oracle_dft(int64_t n, const double *in, double *out, int dir)
         }
         out[2 * k] = acc_r * scale;
         out[2 * k + 1] = acc_i * scale;
+    }
+    return 0;
+}
+
+/* Eq. 1 (dir 0), Eq. 2 (dir 1) or the adjoint (dir 2) at the listed outputs
+ * only: out[b] = scale * sum_j in[j] W^{j * bins[b]}, b < nbins, each summed
+ * term by term like oracle_dft.  Single outputs of transforms too long for
+ * the O(N^2) sum over every output are checked this way. */
+int oracle_dft_bins(int64_t n, const double *in, int64_t nbins, const int64_t *bins, double *out, int dir)
+{
+    if (n < 1 || nbins < 0 || dir < 0 || dir > 2 || !in || !out || (nbins > 0 && !bins)) return -1;
+    const int s = dir_sign(dir);
+    const double scale = dir_scale(dir, n);
+    for (int64_t b = 0; b < nbins; ++b) {
+        const int64_t bin = bins[b];
+        if (bin < 0 || bin >= n) return -1;
+        double sum_r = 0.0, sum_i = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double wr, wi;
+            int64_t e = (int64_t)(((unsigned __int128)j * (unsigned __int128)bin) % (unsigned __int128)n);
+            oracle_w(e, n, s, &wr, &wi);
+            sum_r += in[2 * j] * wr - in[2 * j + 1] * wi;
+            sum_i += in[2 * j] * wi + in[2 * j + 1] * wr;
+        }
+        out[2 * b] = sum_r * scale;
+        out[2 * b + 1] = sum_i * scale;
     }
     return 0;
 }

@@ -262,9 +262,11 @@ def _prec_for(x: torch.Tensor, prec):
 
 
 def fft(x: torch.Tensor, prec=None) -> torch.Tensor:
-    """Eq. 1 over the last dimension: lengths that are powers of two (2..2^28)
-    or products 2^a 3^b 5^c 7^d up to 14336.  complex64 runs in FP32 (or a
-    tensor-core precision), complex128 in FP64 (lengths up to 7168)."""
+    """Eq. 1 over the last dimension.  complex64 runs in FP32 (or a
+    tensor-core precision): powers of two 2..2^28 and products 2^a 3^b 5^c 7^d
+    up to 14336^2 (two passes above 14336).  complex128 runs in FP64: the same
+    7-smooth lengths up to 7168^2 (powers of two up to 2^24; two passes above
+    7168)."""
     _check_input(x, allow_fp64=True)
     return _FFT1d.apply(x, FORWARD, _prec_for(x, prec))
 
@@ -275,15 +277,18 @@ def ifft(x: torch.Tensor, prec=None) -> torch.Tensor:
     return _FFT1d.apply(x, INVERSE, _prec_for(x, prec))
 
 
-def fft2(x: torch.Tensor, prec="fp32") -> torch.Tensor:
-    """2-D transform over the last two dimensions (rows, then columns)."""
-    _check_input(x, 2)
-    return _FFT2d.apply(x, FORWARD, prec)
+def fft2(x: torch.Tensor, prec=None) -> torch.Tensor:
+    """2-D transform over the last two dimensions (rows, then columns).
+    complex64: power-of-two sides up to 2^14 (any precision), or 7-smooth
+    sides up to 14336 in FP32; complex128: 7-smooth sides up to 7168 in FP64."""
+    _check_input(x, 2, allow_fp64=True)
+    return _FFT2d.apply(x, FORWARD, _prec_for(x, prec))
 
 
-def ifft2(x: torch.Tensor, prec="fp32") -> torch.Tensor:
-    _check_input(x, 2)
-    return _FFT2d.apply(x, INVERSE, prec)
+def ifft2(x: torch.Tensor, prec=None) -> torch.Tensor:
+    """Eq. 2 in two dimensions (same sides and precisions as fft2)."""
+    _check_input(x, 2, allow_fp64=True)
+    return _FFT2d.apply(x, INVERSE, _prec_for(x, prec))
 
 
 def fft_many(packed: torch.Tensor, lengths, inverse: bool = False, prec="fp32", tuned: bool = False) -> torch.Tensor:

@@ -28,7 +28,15 @@ struct PassDesc {
 };
 constexpr int kMaxPasses = 4;
 
-enum PlanKind { KIND_SINGLE = 0, KIND_FOURSTEP = 1, KIND_2D = 2, KIND_MANY = 3, KIND_REAL = 4, KIND_MIXED = 5 };
+enum PlanKind {
+  KIND_SINGLE = 0,
+  KIND_FOURSTEP = 1,
+  KIND_2D = 2,
+  KIND_MANY = 3,
+  KIND_REAL = 4,
+  KIND_MIXED = 5,
+  KIND_MIXED_PASSES = 6   // strided mixed-radix passes: four-step 1-D or 2-D (mixed4.cu)
+};
 
 // Lengths N = 2^a 3^b 5^c 7^d that are not powers of two (mixed.cu).
 constexpr int kMixedMaxPasses = 16;
@@ -63,7 +71,42 @@ struct MixedCtInfo {
 const MixedCtInfo* mixed_ct_lookup(long long N);
 
 int mixed_radices(long long N, int* rad);
+bool mixed_schedule(MixedArgs& a, long long N);
 int mixed_plan_init(fft_plan* p);
+
+// Strided passes of the mixed-radix recurrence (mixed4.cu): a batch of
+// sub-transforms of length m.N ("columns") whose element n sits at
+// col * cs + n * ns from the batch's base, C = 2^csh adjacent columns per
+// CTA.  Two such passes make the four-step split of a length beyond one
+// on-chip pass (the column pass multiplies its output by W_Nt^{col * k}) and
+// the rows-then-columns 2-D transform.
+struct Mixed4Args {
+  MixedArgs m;                 // sub-length schedule, W_{m.N} table, in/out, conj and output scale
+  long long in_bs, out_bs;     // element offset of batch b: b * bs
+  long long in_cs, in_ns, out_cs, out_ns;
+  long long ncols;             // columns per batch
+  long long tiles_per_batch;   // ceil(ncols / C)
+  long long ntiles;            // tiles_per_batch * batches
+  const void* ft_lo;           // four-step twiddle W_Nt^e = ft_lo[e & (2^ft_s - 1)] * ft_hi[e >> ft_s]
+  const void* ft_hi;           // of e = col * k on the output (NULL: none)
+  int ft_s;
+};
+struct Mixed4Pass {
+  Mixed4Args a;
+  const void* fn;
+  int threads, smem;
+  long long grid;
+  int in_role, out_role;       // 0 the caller's input, 1 its output, 2 the workspace
+};
+constexpr int kMixed4MaxPasses = 2;
+// kernel for element type (FP64 or FP32), 2^csh columns per CTA, padded index
+const void* mixed4_kernel_fn(bool fp64, int csh, bool pad);
+int mixed4_plan_1d(fft_plan* p);
+int mixed4_plan_2d(fft_plan* p);
+int mixed4_exec(fft_plan* p, const void* in, void* out, int conj, double sx, double sy, int scale_out,
+                cudaStream_t s);
+cudaError_t launch_gen_twiddles_step(void* tab, bool fp64, long long N, long long count, long long step,
+                                     cudaStream_t s);
 int mixed_exec(fft_plan* p, const void* in, void* out, int conj, double sx, double sy, int scale_out,
                cudaStream_t s);
 cudaError_t launch_gen_twiddles_n(float2* tab, long long N, long long count, cudaStream_t s);
@@ -127,6 +170,9 @@ struct fft_plan {
   gbfft::MixedArgs mixed;
   int mixed_threads, mixed_smem, mixed_pad;
   const gbfft::MixedCtInfo* mixed_ct;   // compile-time schedule for this length (FP32), or NULL
+  gbfft::Mixed4Pass m4[gbfft::kMixed4MaxPasses];   // KIND_MIXED_PASSES
+  int m4n;
+  long long m4_n1, m4_n2;   // four-step: column length N1, row length N2 (N = N1 N2); 2-D: ny, nx
   const float2* pre_tw;               // its W_N^n table, n < N/2
   long long tma_grid;                 // its resident-CTA grid
 

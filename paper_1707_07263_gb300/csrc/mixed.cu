@@ -154,6 +154,26 @@ int mixed_radices(long long N, int* rad) {
   return (m == 1) ? n : 0;
 }
 
+// The pass schedule of length N into a: radices, N/R and Ns per pass with
+// their reciprocals, and the twiddle strides into the W_N table.  Returns
+// false when N is not 7-smooth or needs too many passes.
+bool mixed_schedule(MixedArgs& a, long long N) {
+  a.nrad = mixed_radices(N, a.rad);
+  if (a.nrad == 0 || N > kMixedMaxN) return false;
+  a.N = (int)N;
+  unsigned ns = 1;
+  for (int s = 0; s < a.nrad; ++s) {
+    const unsigned nb = (unsigned)(N / a.rad[s]);
+    a.nb[s] = nb;
+    a.nb_m[s] = nb == 1 ? 0u : (unsigned)((0x100000000ULL + nb - 1) / nb);
+    a.ns[s] = ns;
+    a.ns_m[s] = ns == 1 ? 0u : (unsigned)((0x100000000ULL + ns - 1) / ns);
+    ns *= (unsigned)a.rad[s];
+    a.tws[s] = (unsigned)(N / ns);
+  }
+  return true;
+}
+
 int mixed_plan_init(fft_plan* p) {
   MixedArgs& a = p->mixed;
   const long long N = p->n;
@@ -174,24 +194,10 @@ int mixed_plan_init(fft_plan* p) {
     if (h == 128 || h == 256 || h == 512) small_threads = h;
   }
 #endif
-  a.nrad = mixed_radices(N, a.rad);
-  if (a.nrad == 0 || N > (fp64 ? kMixedMaxN64 : kMixedMaxN)) return FFT_ERR_UNSUPPORTED;
-  a.N = (int)N;
+  if (!mixed_schedule(a, N) || N > (fp64 ? kMixedMaxN64 : kMixedMaxN)) return FFT_ERR_UNSUPPORTED;
   a.C = N <= tile ? (int)(tile / N) : 1;
   if (a.C > p->batch) a.C = (int)p->batch;
   a.batch = p->batch;
-  {
-    unsigned ns = 1;
-    for (int s = 0; s < a.nrad; ++s) {
-      const unsigned nb = (unsigned)(N / a.rad[s]);
-      a.nb[s] = nb;
-      a.nb_m[s] = nb == 1 ? 0u : (unsigned)((0x100000000ULL + nb - 1) / nb);
-      a.ns[s] = ns;
-      a.ns_m[s] = ns == 1 ? 0u : (unsigned)((0x100000000ULL + ns - 1) / ns);
-      ns *= (unsigned)a.rad[s];
-      a.tws[s] = (unsigned)(N / ns);
-    }
-  }
   p->mixed_threads = a.C * N <= tile ? small_threads : 512;
   // lengths with a compiled three-pass schedule of composite radices
   // (mixed_ct.cu): their own tile size, CTA size and padding choice

@@ -539,10 +539,13 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
       case KIND_2D: rc = exec_passes(p, fin, fout, dir, s); break;
       case KIND_MANY: rc = many_exec(p, fin, fout, dir, s); break;
       case KIND_REAL: rc = exec_real(p, fin, fout, dir, s); break;
-      case KIND_MIXED: {
+      case KIND_MIXED:
+      case KIND_MIXED_PASSES: {
         const DirXf x = dir_xf(dir, p->n);
         const double sc = (dir & FFT_INVERSE) ? 1.0 / (double)p->n : 1.0;
-        rc = mixed_exec(p, in, out, x.conj, sc, x.conj ? -sc : sc, (x.conj || sc != 1.0) ? 1 : 0, s);
+        const int so = (x.conj || sc != 1.0) ? 1 : 0;
+        rc = p->kind == KIND_MIXED ? mixed_exec(p, in, out, x.conj, sc, x.conj ? -sc : sc, so, s)
+                                   : mixed4_exec(p, in, out, x.conj, sc, x.conj ? -sc : sc, so, s);
         break;
       }
       default: rc = FFT_ERR_INVALID_ARG;
@@ -1032,24 +1035,32 @@ static bool retire(const fft_plan* p) {
 
 extern "C" {
 
-// Lengths that are not powers of two (7-smooth N <= kMixedMaxN, FP32), and
-// every FP64 plan (7-smooth N <= kMixedMaxN64, powers of two included): one
-// pass of the mixed-radix kernel.
+static bool smooth7(int64_t n) {
+  if (n < 1) return false;
+  for (const int f : {2, 3, 5, 7})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+// Lengths that are not powers of two (7-smooth, FP32) and every FP64 plan:
+// one pass of the mixed-radix kernel up to kMixedMaxN (FP32) or kMixedMaxN64
+// (FP64) points, the strided four-step passes of mixed4.cu beyond that (both
+// factors one on-chip pass).
 static fft_plan* create_mixed(int64_t n, int64_t batch, int dir, int prec) {
-  int rad[kMixedMaxPasses];
   const bool fp64 = prec == FFT_PREC_FP64;
   const bool pow2 = n > 0 && (n & (n - 1)) == 0;
   if (n < 2 || batch < 1 || !valid_dir(dir) || !valid_prec(prec) || (double)n * (double)batch > 9.0e15) {
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
   }
-  const bool smooth = pow2 || (n <= kMixedMaxN && mixed_radices(n, rad) != 0);
-  if (!smooth || (!fp64 && n > kMixedMaxN) || (pow2 && n > (1LL << FFT_MAX_LOG2N))) {
+  if (!smooth7(n) || (pow2 && n > (1LL << FFT_MAX_LOG2N))) {
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
   }
-  if (tc_prec(prec) || (fp64 && n > kMixedMaxN64)) {
-    // valid lengths this build does not run at that precision
+  const long long one_pass = fp64 ? kMixedMaxN64 : kMixedMaxN;
+  const long long max_n = one_pass * one_pass;
+  if (tc_prec(prec) || n > max_n) {
+    // valid lengths this build does not run at that precision or size
     set_err(FFT_ERR_UNSUPPORTED);
     return nullptr;
   }
@@ -1063,7 +1074,7 @@ static fft_plan* create_mixed(int64_t n, int64_t batch, int dir, int prec) {
   p->batch = batch;
   p->dir = dir;
   p->prec = prec;
-  const int rc = mixed_plan_init(p);
+  const int rc = n <= one_pass ? mixed_plan_init(p) : mixed4_plan_1d(p);
   if (rc != FFT_OK) {
     free_plan(p);
     set_err(rc);
@@ -1225,15 +1236,46 @@ int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
   return FFT_OK;
 }
 
+// 2-D plans of 7-smooth sides that are not both powers of two, and every FP64
+// 2-D plan: row then column passes of the strided mixed-radix kernel.
+static fft_plan* create_2d_mixed(int64_t ny, int64_t nx, int64_t batch, int dir, int prec) {
+  const long long side_max = prec == FFT_PREC_FP64 ? kMixedMaxN64 : kMixedMaxN;
+  if (tc_prec(prec) || ny > side_max || nx > side_max) {
+    set_err(FFT_ERR_UNSUPPORTED);
+    return nullptr;
+  }
+  fft_plan* p = new_plan();
+  if (!p) {
+    set_err(FFT_ERR_ALLOC);
+    return nullptr;
+  }
+  p->kind = KIND_MIXED_PASSES;
+  p->n = ny * nx;
+  p->ny = ny;
+  p->nx = nx;
+  p->batch = batch;
+  p->dir = dir;
+  p->prec = prec;
+  const int rc = mixed4_plan_2d(p);
+  if (rc != FFT_OK) {
+    free_plan(p);
+    set_err(rc);
+    return nullptr;
+  }
+  return publish(p);
+}
+
 fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int prec) {
   const int ly = ilog2_exact(ny), lx = ilog2_exact(nx);
-  if (ly < 1 || lx < 1 || ly > FFT_MAX_LOG2_SIDE || lx > FFT_MAX_LOG2_SIDE || batch < 1 || !valid_dir(dir) ||
-      !valid_prec(prec)) {
+  if (ny < 2 || nx < 2 || !smooth7(ny) || !smooth7(nx) || batch < 1 || !valid_dir(dir) || !valid_prec(prec) ||
+      (double)ny * (double)nx * (double)batch > 9.0e15) {
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
   }
-  if (prec == FFT_PREC_FP64) {
-    set_err(FFT_ERR_UNSUPPORTED);
+  const bool pow2 = ly >= 1 && lx >= 1;
+  if (prec == FFT_PREC_FP64 || !pow2) return create_2d_mixed(ny, nx, batch, dir, prec);
+  if (ly > FFT_MAX_LOG2_SIDE || lx > FFT_MAX_LOG2_SIDE) {
+    set_err(FFT_ERR_INVALID_ARG);
     return nullptr;
   }
   if (prec != FFT_PREC_FP32) {
@@ -1379,7 +1421,7 @@ int fft_plan_kind(const fft_plan* plan) { return is_live(plan) ? plan->kind : -1
 
 int fft_plan_describe(const fft_plan* p, char* buf, size_t len) {
   if (!is_live(p) || !buf || len == 0) return set_err(FFT_ERR_INVALID_ARG);
-  static const char* kinds[] = {"single", "fourstep", "2d", "many", "real", "mixed", "?", "?"};
+  static const char* kinds[] = {"single", "fourstep", "2d", "many", "real", "mixed", "mixed_passes", "?"};
   snprintf(buf, len,
            "kind=%s n=%lld batch=%lld lg1=%d lg2=%d c1=%d c2=%d threads1=%d smem1=%d threads2=%d smem2=%d "
            "prec=%d launches=%d ws=%zu tma_grid=%lld",

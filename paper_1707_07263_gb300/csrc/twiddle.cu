@@ -75,6 +75,35 @@ cudaError_t launch_gen_twiddles_n64(double2* tab, long long N, long long count, 
   return cudaGetLastError();
 }
 
+// tab[i] = W_N^{(i * step) mod N}, i < count, for any N (the strided
+// mixed-radix plans: sub-length tables with step 1, and the high level of a
+// two-level four-step table with step 2^s); FP64 entries, or rounded once to
+// FP32.
+template <typename T>
+__global__ void gen_twiddles_step(T* tab, long long N, long long count, long long step) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)((i * step) % N) / (double)N, &sn, &cs);
+    if constexpr (sizeof(T) == 16)
+      tab[i] = make_double2(cs, sn);
+    else
+      tab[i] = make_float2((float)cs, (float)sn);
+  }
+}
+
+cudaError_t launch_gen_twiddles_step(void* tab, bool fp64, long long N, long long count, long long step,
+                                     cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const long long blocks = (count + 255) / 256;
+  const unsigned g = (unsigned)(blocks < 4096 ? blocks : 4096);
+  if (fp64)
+    gen_twiddles_step<double2><<<g, 256, 0, s>>>((double2*)tab, N, count, step);
+  else
+    gen_twiddles_step<float2><<<g, 256, 0, s>>>((float2*)tab, N, count, step);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev) {
   const int total = stage_tw_size(lg, rev);
   if (total == 0) return cudaSuccess;

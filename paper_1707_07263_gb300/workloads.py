@@ -55,6 +55,14 @@ def cgauss(n: int, batch: int = 1, seed: int = SEED_BASE) -> np.ndarray:
     return (re + 1j * im).astype(np.complex64)
 
 
+def cgauss128(n: int, batch: int = 1, seed: int = SEED_BASE) -> np.ndarray:
+    """complex128 array (batch, n) with entries CN(0, 1), drawn and kept in FP64
+    (inputs of FP64 transforms)."""
+    g = _rng(seed)
+    s = np.sqrt(0.5)
+    return g.normal(0.0, s, size=(batch, n)) + 1j * g.normal(0.0, s, size=(batch, n))
+
+
 def sar_image(ny: int, nx: int, n_scatterers: int = 64, amplitude: float = 100.0,
               seed: int = SEED_BASE) -> np.ndarray:
     """complex64 (ny, nx) image: CN(0,1) speckle plus ``n_scatterers`` point

@@ -339,6 +339,52 @@ def check_mixed_lengths(lib):
         _close(oracle.transform(d, lib=lib), np.exp(-2j * np.pi * ((k * n0) % n) / n), 1e-12, f"mixed N={n} delta")
 
 
+def check_dft_bins(lib):
+    """Single outputs of long transforms: numpy's pocketfft at powers of two
+    and 7-smooth lengths up to 2^20, every direction, and two closed forms
+    (delayed delta -> W_N^{k n0}; a pure tone -> N at its own bin, 0 at the
+    others) at a length far beyond the O(N^2) route."""
+    for n in (12, 64, 1000, 4096, 100000, 1 << 20):
+        x = _cvec(n, seed=1200 + n % 997)
+        ks = sorted({0, 1, n // 2, n - 1, (7 * n) // 13, (3 * n) // 5 + 1})
+        fwd, inv = np.fft.fft(x), np.fft.ifft(x)
+        _close(oracle.dft_bins(x, ks, oracle.FORWARD, lib=lib), fwd[ks], 1e-12, f"bins N={n} fwd")
+        _close(oracle.dft_bins(x, ks, oracle.INVERSE, lib=lib), inv[ks], 1e-12, f"bins N={n} inv")
+        _close(oracle.dft_bins(x, ks, oracle.ADJOINT, lib=lib), n * inv[ks], 1e-12, f"bins N={n} adj")
+    n = 3 * 5 * 7 * 1024
+    ks = np.array([0, 1, 2, 5, 1000, n // 3, n - 2, n - 1])
+    n0 = 12345
+    d = np.zeros(n, complex)
+    d[n0] = 1
+    _close(oracle.dft_bins(d, ks, lib=lib), np.exp(-2j * np.pi * ((ks * n0) % n) / n), 1e-12, "bins delta")
+    m = 4321
+    tone = np.exp(2j * np.pi * ((np.arange(n) * m) % n) / n)
+    ks2 = np.array([m, m + 1, m - 1, 0, n - 1])
+    want = np.array([n, 0, 0, 0, 0], dtype=complex)
+    err = np.max(np.abs(oracle.dft_bins(tone, ks2, lib=lib) - want))
+    assert err <= 1e-9 * n, f"bins tone: {err:.3e}"
+    # batched rows keep their own outputs
+    xb = _cvec(360, seed=1299, batch=3)
+    _close(oracle.dft_bins(xb, [5, 17], lib=lib), np.fft.fft(xb, axis=-1)[:, [5, 17]], 1e-12, "bins batched")
+
+
+def check_fft2_mixed(lib):
+    """2-D transforms with sides that are not powers of two: numpy's fft2 /
+    ifft2 and the separable delta closed form."""
+    for ny, nx in ((12, 20), (3, 64), (35, 6)):
+        g = _rng(ny * 100 + nx)
+        x = g.standard_normal((2, ny, nx)) + 1j * g.standard_normal((2, ny, nx))
+        _close(oracle.fft2(x, oracle.FORWARD, lib=lib), np.fft.fft2(x), 1e-13, f"fft2 {ny}x{nx}")
+        _close(oracle.fft2(x, oracle.INVERSE, lib=lib), np.fft.ifft2(x), 1e-13, f"ifft2 {ny}x{nx}")
+        d = np.zeros((ny, nx), complex)
+        y0, x0 = ny // 3 + 1, nx // 5 + 1
+        d[y0, x0] = 1
+        ky, kx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        ref = np.exp(-2j * np.pi * (((ky * y0) % ny) / ny + ((kx * x0) % nx) / nx))
+        _close(oracle.fft2(d, lib=lib), ref, 1e-13, f"fft2 delta {ny}x{nx}")
+
+
 ALL_CHECKS = (check_golden, check_small_by_hand, check_closed_forms, check_invariants,
               check_dft_vs_fft, check_numpy, check_fft2, check_range_compress, check_real_transforms,
-              check_mixed_lengths, check_golden_real_and_filter, check_golden_mixed)
+              check_mixed_lengths, check_golden_real_and_filter, check_golden_mixed, check_dft_bins,
+              check_fft2_mixed)

@@ -51,7 +51,7 @@ def test_error_strings(lib):
 @pytest.mark.parametrize("n,batch,dir,prec", [
     (11, 1, 0, 0),        # a prime factor above 7
     (2 * 3 * 7 * 11, 1, 0, 0),
-    (3 << 13, 1, 0, 0),   # 7-smooth but beyond the one-pass mixed-radix limit (14336)
+    (13 * 1024, 1, 0, 0), # prime factor 13 beyond one on-chip pass
     (0, 1, 0, 0),
     (1, 1, 0, 0),         # N=1 is not supported
     (-8, 1, 0, 0),
@@ -73,7 +73,9 @@ def test_mixed_radix_tensor_core_is_unsupported(lib):
 
 
 def test_plan_create_2d_rejects(lib):
-    assert lib.fft_plan_create_2d(12, 16, 1, 0, 0) is None
+    assert lib.fft_plan_create_2d(11, 16, 1, 0, 0) is None    # prime side
+    assert lib.fft_plan_create_2d(16, 26, 1, 0, 0) is None    # side with factor 13
+    assert lib.fft_plan_create_2d(1, 16, 1, 0, 0) is None
     assert lib.fft_plan_create_2d(16, 1 << 15, 1, 0, 0) is None
     assert lib.fft_plan_create_2d(16, 16, 0, 0, 0) is None
     assert lib.fft_last_error() == -1
@@ -189,17 +191,27 @@ def test_autotune_rejects_before_running(lib):
 
 
 def test_fp64_and_mixed_length_limits(lib):
+    """Argument errors (-1) and valid requests beyond what is built (-6), all
+    decided on the host before any device work."""
     from paper_1707_07263_gb300 import _lib
     fp64 = _lib.FFT_PREC_FP64
-    assert lib.fft_plan_create(8192, 1, 0, fp64) is None        # power of two beyond one FP64 pass
+    assert lib.fft_plan_create(1 << 25, 1, 0, fp64) is None     # 4096 x 8192: no split into two FP64 passes
+    assert lib.fft_last_error() == -6
+    assert lib.fft_plan_create(7168 * 7168 * 2, 1, 0, fp64) is None   # beyond two FP64 passes
+    assert lib.fft_last_error() == -6
+    assert lib.fft_plan_create(3 ** 17, 1, 0, 0) is None        # 7-smooth, no split into two passes of <= 14336
+    assert lib.fft_last_error() == -6
+    assert lib.fft_plan_create(14336 * 14336 * 3, 1, 0, 0) is None   # beyond two mixed-radix passes
     assert lib.fft_last_error() == -6
     assert lib.fft_plan_create(13 * 16, 1, 0, fp64) is None     # prime factor 13
     assert lib.fft_last_error() == -1
     assert lib.fft_plan_create(1, 1, 0, fp64) is None
     assert lib.fft_last_error() == -1
-    assert lib.fft_plan_create(14337, 1, 0, 0) is None          # beyond the mixed-radix limit
+    assert lib.fft_plan_create(14337, 1, 0, 0) is None          # 3^5 * 59
     assert lib.fft_last_error() == -1
-    assert lib.fft_plan_create_2d(64, 64, 1, 0, fp64) is None   # FP64 2-D is not built
+    assert lib.fft_plan_create_2d(64, 8192, 1, 0, fp64) is None     # FP64 side beyond one pass
+    assert lib.fft_last_error() == -6
+    assert lib.fft_plan_create_2d(12, 16, 1, 0, 1) is None      # mixed 2-D on the tensor cores
     assert lib.fft_last_error() == -6
     arr = (ctypes.c_int64 * 2)(16, 32)
     assert lib.fft_plan_create_many(arr, 2, 0, fp64) is None

@@ -1,6 +1,7 @@
-"""FP64 (complex128) transforms against the FP64 oracle on the same seeded
-inputs: powers of two up to 4096 and 7-smooth lengths up to 7168, every
-direction, in place, the gradient, and the limits.
+"""FP64 (complex128) one-pass transforms against the FP64 oracle on the same
+seeded inputs: powers of two up to 4096 and 7-smooth lengths up to 7168, every
+direction, in place, the gradient, and the limits (the two-pass FP64 lengths
+and FP64 2-D are in test_gpu_mixed_passes.py).
 
 Bar: relative L2 error of every transform <= 5e-15 * log2(N) + 2e-16 * sqrt(N):
 FP64 arithmetic with twiddles correct to an ulp gives errors of order
@@ -93,14 +94,16 @@ def test_api_complex128_and_gradient():
 
 def test_limits():
     lib = L.load()
-    assert lib.fft_plan_create(8192, 1, 0, L.FFT_PREC_FP64) is None       # beyond one FP64 pass
-    assert lib.fft_last_error() == -6
-    assert lib.fft_plan_create(7200, 1, 0, L.FFT_PREC_FP64) is None       # 7-smooth, beyond 7168
+    assert lib.fft_plan_create(1 << 25, 1, 0, L.FFT_PREC_FP64) is None    # no split into two FP64 passes
     assert lib.fft_last_error() == -6
     assert lib.fft_plan_create(11, 1, 0, L.FFT_PREC_FP64) is None         # prime factor above 7
     assert lib.fft_last_error() == -1
-    assert lib.fft_plan_create_2d(64, 64, 1, 0, L.FFT_PREC_FP64) is None
+    assert lib.fft_plan_create_2d(64, 7200, 1, 0, L.FFT_PREC_FP64) is None  # side beyond one FP64 pass
     assert lib.fft_last_error() == -6
+    for n in (8192, 7200):                                                   # two passes from 7169 on
+        h = ctypes.c_void_p(lib.fft_plan_create(n, 1, 0, L.FFT_PREC_FP64))
+        assert h.value and lib.fft_plan_kind(h) == 6
+        lib.fft_destroy(h)
     h = ctypes.c_void_p(lib.fft_plan_create(1024, 2, 0, L.FFT_PREC_FP64))
     buf = torch.zeros(2 * 1024 + 1, dtype=torch.complex128, device="cuda")
     p8 = ctypes.c_void_p(buf.data_ptr() + 8)

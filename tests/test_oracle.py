@@ -84,6 +84,8 @@ MUTATIONS = {
     "no_inverse_scale": ("return dir == 1 ? 1.0 / (double)n : 1.0;", "return 1.0;"),
     "transposed_2d": ("col[2 * y] = out[2 * (y * nx + x)];", "col[2 * y] = out[2 * (x * ny + y)];"),  # in bounds
     "swapped_halves": ("fft_rec(h, x, 2 * stride, y, s);", "fft_rec(h, x + 2 * stride, 2 * stride, y, s);"),
+    "bins_wrong_output": ("(unsigned __int128)j * (unsigned __int128)bin)", "(unsigned __int128)j * (unsigned __int128)b)"),
+    "bins_dropped_term": ("sum_r += in[2 * j] * wr - in[2 * j + 1] * wi;", "sum_r += in[2 * j] * wr;"),
 }
 
 
