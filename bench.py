@@ -30,7 +30,8 @@ Also printed on the same JSON line:
 
 ``--impl reference`` times the oracle instead (the deliberately slow CPU
 baseline) and prints the same line with "impl": "reference".
-Other workloads for measurement only: --workload large | tc | many | range | real | mixed | fp64.
+Other workloads for measurement only: --workload large | tc | many | range | real | mixed | fp64 |
+passes.
 """
 from __future__ import annotations
 
@@ -1117,6 +1118,57 @@ def run_measure(args):
             lib.fft_destroy(h)
         desc = ("FP64 (complex128) transforms, one on-chip pass: 2^25 CN(0,1) points per launch; HBM fraction "
                 "counts 32 B per point; cufft_torch = torch.fft on complex128 (context)")
+    elif args.workload == "passes":
+        # two strided mixed-radix passes: FP64 lengths beyond one pass (2^25 points per launch) and
+        # FP32 mixed-radix lengths beyond 14336 (~2^26 points), 1-D and 2-D
+        cases = [(1 << 13, None, 5), (1 << 16, None, 5), (1 << 20, None, 5), (1 << 24, None, 5), (10000, None, 5),
+                 (10 ** 6, None, 5), (1024, 1024, 5), (15000, None, 0), (16000, None, 0), (10 ** 6, None, 0),
+                 (1000, 1000, 0)]
+        for n, ny, prec in cases:
+            fp64 = prec == _lib.FFT_PREC_FP64
+            pts = (1 << 25) if fp64 else TOTAL
+            img = n * (ny or 1)
+            batch = max(1, pts // img)
+            gen = workloads.cgauss128 if fp64 else workloads.cgauss
+            xh = gen(img, batch, seed=workloads.seed_for(10) + img)
+            x = torch.from_numpy(xh.reshape(-1)).to(dev)
+            y = torch.empty_like(x)
+            if ny:
+                h = ctypes.c_void_p(lib.fft_plan_create_2d(ny, n, batch, 0, prec))
+                wsb = None
+            else:
+                h, wsb = plan(n, batch, prec)
+            us = _time_fn(torch, lambda: run_plan(h, x, y), args.steps, args.warmup, stream) * 1e3
+            shape = (batch, ny, n) if ny else (batch, n)
+
+            def cufft():
+                with torch.cuda.stream(stream):
+                    (torch.fft.fft2 if ny else torch.fft.fft)(x.view(*shape))
+
+            cu = _time_fn(torch, cufft, args.steps, args.warmup, stream) * 1e3
+            run_plan(h, x, y)
+            torch.cuda.synchronize()
+            if ny:
+                err = None
+                if n & (n - 1) == 0 and ny & (ny - 1) == 0:
+                    got = y.view(*shape)[:1].cpu().numpy()
+                    err = float(oracle.rel_l2(got, oracle.fft2(xh.reshape(shape)[:1].astype(np.complex128))))
+            else:
+                ks = np.array([0, 1, n // 3, n - 1])
+                got = y.view(*shape)[[0, batch - 1]][:, ks].cpu().numpy()
+                err = float(oracle.rel_l2_rows(got, oracle.dft_bins(xh[[0, batch - 1]].astype(np.complex128),
+                                                                    ks)).max())
+            N = img
+            res.append({"n": n, "ny": ny, "batch": batch, "prec": "fp64" if fp64 else "fp32", "us": round(us, 1),
+                        "cufft_torch_us": round(cu, 1),
+                        "gflops": round(5.0 * N * np.log2(N) * batch / (us * 1e-6) / 1e9, 1),
+                        "hbm_frac": round((32.0 if fp64 else 16.0) * N * batch / (us * 1e-6) / 1e9 / peak, 4),
+                        "err_sampled": None if err is None else float(f"{err:.3e}")})
+            lib.fft_destroy(h)
+            del wsb
+        desc = ("two strided mixed-radix passes (four-step N = N1 N2, or rows then columns): FP64 complex128 "
+                "2^25 points per launch, FP32 ~2^26; errors at sampled outputs (term-by-term oracle sums) or "
+                "whole images; cufft_torch = torch.fft (context)")
     print(json.dumps({"workload": args.workload, "desc": desc, "results": res,
                       "peak_hbm_gbs": peak}), flush=True)
 
@@ -1127,7 +1179,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range", "real", "mixed", "fp64"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range", "real", "mixed", "fp64",
+                                                          "passes"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

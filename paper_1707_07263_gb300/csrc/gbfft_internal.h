@@ -99,6 +99,14 @@ struct Mixed4Pass {
   int in_role, out_role;       // 0 the caller's input, 1 its output, 2 the workspace
 };
 constexpr int kMixed4MaxPasses = 2;
+// FP32 sub-lengths with a compile-time schedule (mixed4_ct.cu)
+struct Mixed4CtInfo {
+  long long L;
+  int r0, r1, r2;  // radices (r2 == 1: two passes)
+  int csh;         // 2^csh columns per CTA
+  const void* fn;  // kernel void(Mixed4Args)
+};
+const Mixed4CtInfo* mixed4_ct_lookup(long long L);
 // kernel for element type (FP64 or FP32), 2^csh columns per CTA, padded index
 const void* mixed4_kernel_fn(bool fp64, int csh, bool pad);
 int mixed4_plan_1d(fft_plan* p);

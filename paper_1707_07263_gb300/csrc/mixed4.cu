@@ -47,15 +47,20 @@ static int m4_pass_init(fft_plan* p, Mixed4Pass& P, long long L, long long ncols
   Mixed4Args& a = P.a;
   if (!mixed_schedule(a.m, L)) return FFT_ERR_UNSUPPORTED;
   a.m.tw = tw;
+  // FP32 sub-lengths with a compiled schedule take it when the batch has
+  // at least its columns per CTA
+  const Mixed4CtInfo* ct = fp64 ? nullptr : mixed4_ct_lookup(L);
+  if (ct && (1LL << ct->csh) > ncols) ct = nullptr;
   const long long target = fp64 ? 2048 : 4096;
   const int csh_max = fp64 ? 3 : 4;
   int csh = 0;
   while (csh < csh_max && (L << (csh + 1)) <= target && (2LL << csh) <= ncols) ++csh;
   while (csh > 0 && m4_smem(L, csh, true, esz) > kMixed4SmemLimit) --csh;
+  if (ct) csh = ct->csh;
   const bool pad = m4_smem(L, csh, true, esz) <= kMixed4SmemLimit;
   const size_t smem = m4_smem(L, csh, pad, esz);
-  if (smem > kMixed4SmemLimit) return FFT_ERR_UNSUPPORTED;
-  P.fn = mixed4_kernel_fn(fp64, csh, pad);
+  if (smem > kMixed4SmemLimit || (ct && !pad)) return FFT_ERR_UNSUPPORTED;
+  P.fn = ct ? ct->fn : mixed4_kernel_fn(fp64, csh, pad);
   if (!P.fn) return FFT_ERR_UNSUPPORTED;
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(P.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -132,18 +137,24 @@ static int m4_tables(fft_plan* p, long long La, long long Lb, long long Nft, M4T
 }
 
 // N = N1 N2 with N1 the largest divisor of N at most sqrt(N) whose cofactor
-// is one on-chip sub-transform.
+// is one on-chip sub-transform; in FP32 the largest such N1 for which both
+// lengths have a compiled schedule, when there is one.
 int mixed4_plan_1d(fft_plan* p) {
   const bool fp64 = p->prec == FFT_PREC_FP64;
   const long long N = p->n, Lmax = fp64 ? kMixedMaxN64 : kMixedMaxN;
-  long long n1 = 0;
+  long long n1 = 0, n1_ct = 0;
   long long d = (long long)std::sqrt((double)N) + 1;
   while (d * d > N) --d;
-  for (; d >= 2; --d)
-    if (N % d == 0 && N / d <= Lmax) {
-      n1 = d;
+  for (; d >= 2; --d) {
+    if (N % d != 0 || N / d > Lmax) continue;
+    if (n1 == 0) n1 = d;
+    if (!fp64 && mixed4_ct_lookup(d) && mixed4_ct_lookup(N / d)) {
+      n1_ct = d;
       break;
     }
+    if (fp64) break;
+  }
+  if (n1_ct) n1 = n1_ct;
   if (n1 == 0) return FFT_ERR_UNSUPPORTED;
   const long long n2 = N / n1;
   M4Tables t;

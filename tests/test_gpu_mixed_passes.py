@@ -241,6 +241,23 @@ def test_fp32_mixed_2d(ny, nx):
     assert err <= tol32(ny * nx), f"{ny}x{nx}: {err:.2e}"
 
 
+# every sub-length with a compiled schedule, as the column pass of a 2-D plan
+# (ny x nx images, nx a multiple of 3 and at least the schedule's columns per
+# CTA, so that the plan is a mixed-radix one; the rows of nx points run on the
+# run-time kernel)
+COMPILED = [64, 100, 120, 125, 128, 160, 200, 240, 250, 256, 320, 400, 500, 512, 625, 1000, 1024, 1250, 2000,
+            2048, 2500, 3125, 4000, 4096]
+
+
+@pytest.mark.parametrize("ny", COMPILED)
+def test_fp32_compiled_sub_lengths(ny):
+    nx = 48 if ny <= 256 else (24 if ny <= 512 else 12)
+    batch = 2 if ny < 1000 else 1
+    x = workloads.cgauss(ny * nx, batch, seed=10550 + ny).reshape(batch, ny, nx)
+    err = err2d(run2d(x, 0, L.FFT_PREC_FP32), ref2d(x, 0))
+    assert err <= tol32(ny * nx), f"{ny}x{nx}: {err:.2e}"
+
+
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_fp32_mixed_2d_directions_in_place(d):
     ny, nx = 30, 96
