@@ -134,9 +134,12 @@ GBFFT_API fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, in
  * transform of length n/2 and one split step give the result.  n <= 2^15: one
  * fused kernel, one read and one write of every value.  2^16 <= n <= 2^19,
  * real to complex: the complex plan's column pass, then its row pass with the
- * split folded in (rows k1 and n/2/N1 - k1 in one tile), two passes.  Other
- * longer n and directions: the complex plan plus one split kernel.  Multi-pass
- * lengths need a workspace (fft_plan_workspace_bytes).
+ * split folded in (rows k1 and n/2/N1 - k1 in one tile), two passes.
+ * 2^16 <= n <= 2^21, complex to real: the split folded into the complex
+ * plan's column pass (X[m] and X[n/2 - m] read from the same row), then its
+ * row pass, two passes.  Other longer n and directions: the complex plan plus
+ * one split kernel.  Multi-pass lengths need a workspace
+ * (fft_plan_workspace_bytes).
  * The adjoints (for backpropagation; adjoint with respect to the real inner
  * product <u, v> = Re sum conj(u) v, which is PyTorch's gradient convention):
  *   FFT_ADJOINT (adjoint of FFT_FORWARD): in = rows of n/2 + 1 complex64 g,
@@ -316,7 +319,8 @@ GBFFT_API int fft_plan_set_workspace(fft_plan* plan, void* dev_ptr);
 GBFFT_API int64_t fft_plan_length(const fft_plan* plan);
 GBFFT_API int64_t fft_plan_batch(const fft_plan* plan);
 /* Number of kernel launches one fft_exec issues (real-data plans: the largest
- * of the directions; the folded real-to-complex direction issues one fewer). */
+ * of the directions; a folded direction issues one fewer than the complex
+ * plan plus a split kernel). */
 GBFFT_API int fft_plan_launches(const fft_plan* plan);
 /* Kind: 0 single on-chip pass, 1 four-step, 2 two-dimensional, 3 uneven batch,
  * 4 real data, 5 mixed radix (one pass), 6 two strided mixed-radix passes

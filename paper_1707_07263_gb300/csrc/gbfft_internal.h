@@ -127,6 +127,9 @@ cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, lon
 // (real_fold.cu).
 struct TileKernelInfo;
 const TileKernelInfo* r2c_fold_kernel_info(int lg2);
+// complex to real: the split folded into the inner column pass (columns of
+// 2^lg1 points, C per CTA), or NULL
+const TileKernelInfo* c2r_fold_kernel_info(int lg1, int C);
 int r2c_fold_launch(const TileKernelInfo* k, const TileArgs& a, long long M, int N1, long long batch,
                     const float2* r_lo, const float2* r_hi, int r_s, int scale, float s_int, float s_end,
                     cudaStream_t s);
@@ -167,6 +170,7 @@ struct fft_plan {
   const gbfft::TileKernelInfo* kr2c;
   const gbfft::TileKernelInfo* kc2r;
   const gbfft::TileKernelInfo* krfold;   // real-to-complex: split folded into the inner row pass (or NULL)
+  const gbfft::TileKernelInfo* kcfold;   // complex-to-real: split folded into the inner column pass (or NULL)
   fft_plan* inner;
   void* d_rtw;        // W_N^k, k < M, two-level: r_lo[k & (2^r_s - 1)] * r_hi[k >> r_s]
   const float2* r_lo;

@@ -503,6 +503,32 @@ static int exec_real(fft_plan* p, const float2* in, float2* out, int dir, cudaSt
     return r2c_fold_launch(p->krfold, b, M, 1 << q->lg1, p->batch, p->r_lo, p->r_hi, p->r_s, adj ? 1 : 0, s_int,
                            s_end, s);
   }
+  if (!to_complex && p->kcfold) {
+    // the inner plan's column pass with the split folded in, reading the rows
+    // of M + 1 values, then its row pass
+    const fft_plan* q = p->inner;
+    if (!q->ws) return FFT_ERR_NO_WORKSPACE;
+    const PassDesc& A = q->pass[0];
+    TileArgs a = A.a;
+    a.in = in;
+    a.out = (float2*)q->ws;
+    a.in_bstride = M + 1;
+    a.r_w = p->r_lo;
+    a.r_hi = p->r_hi;
+    a.r_s = p->r_s;
+    a.r_end2 = adj ? 1 : 0;
+    a.conj_in = 1;   // the inverse as conj(F(conj Z))
+    int rc = launch_tile(p->kcfold, a, A.ntiles, s);
+    if (rc) return rc;
+    const PassDesc& B = q->pass[1];
+    TileArgs b = B.a;
+    b.in = (const float2*)q->ws;
+    b.out = out;
+    b.scale_out = 1;
+    b.sx = adj ? 1.0f : (float)(1.0 / (double)M);
+    b.sy = -b.sx;
+    return launch_tile(B.k, b, B.ntiles, s);
+  }
   if (to_complex) {
     const int rc = exec_plan(p->inner, in, p->zbuf, FFT_FORWARD, s);
     if (rc) return rc;
@@ -1165,6 +1191,14 @@ static int plan_real(fft_plan* p, int lgN) {
     const int rc = prepare_kernel(p->krfold);
     if (rc) return rc;
   }
+  // ... and the complex-to-real split inside the column pass
+  if (q->kind == KIND_FOURSTEP && q->npass == 2 && !q->fused && q->pass[0].k && q->pass[0].k->map == MAP_CC &&
+      c2r_fold_kernel_info(q->lg1, q->pass[0].k->C)) {
+    p->kcfold = c2r_fold_kernel_info(q->lg1, q->pass[0].k->C);
+    const int rc = prepare_kernel(p->kcfold);
+    if (rc) return rc;
+  }
+  if (p->krfold && p->kcfold) p->launches = p->inner->launches;   // both directions folded
   p->lg2 = p->inner->lg2;
   p->d_status = p->inner->d_status;
   p->ws_bytes = align256(p->inner->ws_bytes) + (size_t)M * (size_t)p->batch * 8;

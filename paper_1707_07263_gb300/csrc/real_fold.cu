@@ -1,7 +1,8 @@
-// real_fold.cu -- real-to-complex transforms of N = 2M reals with M = N1 * N2
-// a two-pass four-step length (2^15..2^18): the even/odd split folded into the
-// row pass of the complex transform, so that the transform takes two passes
-// over memory instead of three.
+// real_fold.cu -- real-data transforms of N = 2M reals with M = N1 * N2 a
+// two-pass four-step length (2^15..2^18): the even/odd split folded into the
+// row pass of the complex transform (real to complex) or into its column pass
+// (complex to real), so that the transform takes two passes over memory
+// instead of three.
 //
 // The row of N reals is read as M complex values z[m] = x[2m] + i x[2m+1]
 // (Sec. 2.1's even/odd split) and Z = Eq. 1 of z (length M) is computed by the
@@ -101,6 +102,30 @@ const TileKernelInfo* r2c_fold_kernel_info(int lg2) {
   static const TileKernelInfo tab[] = {GBFFT_FOLD(6), GBFFT_FOLD(7), GBFFT_FOLD(8), GBFFT_FOLD(9), GBFFT_FOLD(10)};
   if (lg2 < 6 || lg2 > 10) return nullptr;
   return &tab[lg2 - 6];
+}
+
+// Complex-to-real transforms of the same lengths: the split that builds
+// Z[m] = E + i O from X[m] and X[M - m] runs inside the column pass of the
+// inverse complex transform (tile_fft.cuh, first-pass mode 7), which reads X
+// straight from the rows of M + 1 values; X[M - m] lies in the mirror column
+// N2 - n2 of the same transform, usually an L2 hit.  The column pass then
+// continues as the complex plan's own (four-step twiddle, workspace), and the
+// row pass is the complex plan's.
+template <int LG1>
+__global__ void __launch_bounds__(TileCfg<LG1, kFoldCols, true, true>::T) c2r_fold_kernel(const TileArgs a) {
+  extern __shared__ float2 smem[];
+  tile_body<LG1, kFoldCols, true, true, false, 7>(a, (long long)blockIdx.x, smem);
+}
+
+#define GBFFT_CFOLD(LG) \
+  {(const void*)&c2r_fold_kernel<LG>, TileCfg<LG, kFoldCols, true, true>::T, \
+   TileCfg<LG, kFoldCols, true, true>::SMEM_BYTES, LG, kFoldCols, MAP_CC}
+
+// The folded column kernel for columns of 2^lg1 points, C per CTA, or NULL.
+const TileKernelInfo* c2r_fold_kernel_info(int lg1, int C) {
+  static const TileKernelInfo tab[] = {GBFFT_CFOLD(7), GBFFT_CFOLD(8)};
+  if (C != kFoldCols || lg1 < 7 || lg1 > 8) return nullptr;
+  return &tab[lg1 - 7];
 }
 
 int r2c_fold_launch(const TileKernelInfo* k, const TileArgs& a, long long M, int N1, long long batch,

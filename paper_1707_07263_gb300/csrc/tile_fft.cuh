@@ -37,6 +37,7 @@
 #include <stdint.h>
 
 #include "../../include/gbfft.h"
+#include "ct_trig.h"
 #include "fft_common.cuh"
 #include "tma_util.cuh"
 
@@ -189,6 +190,10 @@ struct TileArgs {
   // takes scale_out: outputs X[1..L-1] times sx, X[0] and X[L] times sy (the
   // adjoint of the complex-to-real transform has sx = 2/N, sy = 1/N).
   int r_end2;
+  // Complex-to-real split folded into a four-step column pass (PRE == 7):
+  // W_N^m = r_w[m & (2^r_s - 1)] * r_hi[m >> r_s], m < M (two levels).
+  const float2* r_hi;
+  int r_s;
 };
 
 // Filter value of range compression at frequency index k (conjugated for the
@@ -196,6 +201,23 @@ struct TileArgs {
 __device__ __forceinline__ float2 filt_at(const TileArgs& a, long long k) {
   const float2 f = __ldg(a.filt + k);
   return a.filt_conj ? make_float2(f.x, -f.y) : f;
+}
+
+// Z[m] = E + i O of a complex-to-real split for the R inputs
+// m = m0 + r M/R of one butterfly: E = (X[m] + conj X[M-m]) / 2,
+// O = (X[m] - conj X[M-m]) conj(W_N^m) / 2, with W_N^m = w0 W_{2R}^r
+// (W_{2R}^r = exp(-i pi r / R) as compile-time constants).
+template <int R, int r = 0>
+__device__ __forceinline__ void c2r_combine(float2* v, const float2* x1, const float2* x2, float2 w0) {
+  if constexpr (r < R) {
+    constexpr float hc = (float)ct_cos(r, 2 * R), hs = (float)ct_sin(r, 2 * R);
+    const float2 w = cmul(w0, make_float2(hc, -hs));   // hs = sin(pi r / R)
+    const float2 e = make_float2(0.5f * (x1[r].x + x2[r].x), 0.5f * (x1[r].y - x2[r].y));
+    const float2 d = make_float2(0.5f * (x1[r].x - x2[r].x), 0.5f * (x1[r].y + x2[r].y));
+    const float2 o = cmul(d, make_float2(w.x, -w.y));
+    v[r] = make_float2(e.x - o.y, e.y + o.x);
+    c2r_combine<R, r + 1>(v, x1, x2, w0);
+  }
 }
 
 template <int R>
@@ -229,7 +251,10 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 //        5: first pass builds Z[n] = E[n] + i O[n] of a complex-to-real
 //        transform from X[n] and X[L - n] of rows of L + 1 values (C2R);
 //        6: first pass reads an unpadded copy of the C rows that a bulk copy
-//        left at the start of the exchange buffer `sm` (tile_fft_pfs_kernel).
+//        left at the start of the exchange buffer `sm` (tile_fft_pfs_kernel);
+//        7: as 5 for the column pass of a four-step complex-to-real plan:
+//        element m = n1 N2 + n2 of the length-M input (n1 down the column,
+//        n2 = col0 + c, M = L * ncols) is built from X[m] and X[M - m].
 //   POST 0: last pass stores to global memory; 2: last pass multiplies output
 //        k by filt[k] and conjugates it, in registers; 3: last pass leaves
 //        output k in shared memory at sidx(k) (natural order) and splits the
@@ -313,6 +338,30 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
           const float2 o = cmul(d, make_float2(w[r].x, -w[r].y));
           v[i * R + r] = make_float2(e.x - o.y, e.y + o.x);
         }
+      } else if constexpr (PRE == 7) {
+        // the same split down a column: X[m] and X[M - m] lie in mirror
+        // columns (N2 - n2), read straight from the rows of M + 1 values;
+        // W_N^m from the two-level table
+        // (the step between the R inputs is M / R, so W_N^{m0 + r M/R} =
+        // W_N^{m0} W_{2R}^r: one table product per butterfly, then constants)
+        static_assert(IN_CF && !OFFS, "complex-to-real column pass");
+        const long long M = (long long)L * a.ncols;
+        const long long m0 = col0 + cc[i] + (long long)jj[i] * isn;   // m of r = 0
+        const float2* pm = p + (M - 2 * m0);                            // X[M - m] = pm[-r * step]
+        const unsigned lo_mask = (1u << a.r_s) - 1u;
+        const float2 w0 = cmul(__ldg(a.r_w + ((unsigned)m0 & lo_mask)), __ldg(a.r_hi + ((unsigned)m0 >> a.r_s)));
+        float2 x1[R], x2[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          x1[r] = ok ? __ldg(p + r * step) : make_float2(0.f, 0.f);
+          x2[r] = ok ? __ldg(pm - r * step) : make_float2(0.f, 0.f);
+        }
+        if (m0 == 0) {   // m == 0 only for r == 0
+          const float em = (float)(1 + a.r_end2);
+          x1[0] = make_float2(x1[0].x * em, 0.f);
+          x2[0] = make_float2(x2[0].x * em, 0.f);
+        }
+        c2r_combine<R>(v + i * R, x1, x2, w0);
       } else if constexpr (PRE == 2) {
         // column tile already staged in shared memory by a tensor TMA copy,
         // laid out [n][c] (gin points at it)
@@ -542,7 +591,7 @@ __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT
 // One tile of a pass: tile index `tile` of the launch described by `a`, using
 // `smem` (TileCfg::SMEM_BYTES).  Shared by the one-tile-per-CTA kernel below
 // and the persistent uneven-batch kernel.
-template <int LG, int C, bool IN_CF, bool OUT_CF, bool OFFS = false>
+template <int LG, int C, bool IN_CF, bool OUT_CF, bool OFFS = false, int PRE = 0>
 __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, float2* smem) {
   using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
   float2* sm = smem;
@@ -574,7 +623,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, flo
   }
 
   float2 v[Cfg::P];
-  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS>(v, sm, a, gin, gout, col0, b, epi_tab);
+  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS, PRE>(v, sm, a, gin, gout, col0, b, epi_tab);
 }
 
 // Two CTAs per transform of length 2^(LG+1) (radix-2 decimation in

@@ -54,7 +54,8 @@ def test_rfft_matches_oracle(lg):
     assert oracle.rel_l2_rows(got, ref).max() <= tol(n), f"N=2^{lg}"
 
 
-@pytest.mark.parametrize("lg", list(range(2, 16)) + [16, 17, 20])
+# 2^16..2^21: the split folded into the column pass of the complex plan
+@pytest.mark.parametrize("lg", list(range(2, 16)) + [16, 17, 18, 19, 20, 21])
 def test_irfft_matches_oracle(lg):
     """Random half spectra, including nonzero Im X[0] and Im X[N/2], which the
     transform must ignore."""
@@ -88,14 +89,18 @@ def test_large_sampled(lg):
     assert oracle.rel_l2_rows(got2, oracle.irfft(X.astype(np.complex128), n)).max() <= tol(n)
 
 
-@pytest.mark.parametrize("lg,batch", [(13, 8192), (15, 2048)])
+@pytest.mark.parametrize("lg,batch", [(13, 8192), (15, 2048), (16, 1024)])
 def test_full_size_sampled(lg, batch):
-    """The shapes of the real-data workload (2^26 reals), rows sampled."""
+    """The shapes of the real-data workload (2^26 reals), both directions,
+    rows sampled."""
     n = 1 << lg
     x = real_rows(n, batch, seed=6400 + lg)
     got = gb.rfft(torch.from_numpy(x).cuda()).cpu().numpy()
     rows = np.concatenate([np.random.Generator(np.random.PCG64(lg)).choice(batch, 16, replace=False), [0, batch - 1]])
     assert oracle.rel_l2_rows(got[rows], oracle.rfft(x[rows].astype(np.float64))).max() <= tol(n)
+    X = half_spectrum(n, batch, seed=6450 + lg)
+    back = gb.irfft(torch.from_numpy(X).cuda(), n).cpu().numpy()
+    assert oracle.rel_l2_rows(back[rows], oracle.irfft(X[rows].astype(np.complex128), n)).max() <= tol(n)
 
 
 def test_rfft_gradient():
@@ -138,7 +143,7 @@ def test_irfft_gradient_finite_differences():
     assert oracle.rel_l2(Xt.grad.cpu().numpy(), fd) <= 1e-5
 
 
-@pytest.mark.parametrize("lg", [2, 3, 5, 8, 11, 12, 15, 16, 18])
+@pytest.mark.parametrize("lg", [2, 3, 5, 8, 11, 12, 15, 16, 18, 21])
 def test_real_adjoints_match_oracle(lg):
     """The adjoints of the real transforms (FFT_ADJOINT and FFT_INVERSE |
     FFT_ADJOINT on a real plan) against their definitions written with the
