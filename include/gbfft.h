@@ -132,7 +132,7 @@ GBFFT_API fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, in
  * The row of n reals is read as n/2 complex values x[2m] + i x[2m+1] (Sec. 2.1
  * splits a sequence into even and odd samples the same way); one complex
  * transform of length n/2 and one split step give the result.  n <= 2^15: one
- * fused kernel, one read and one write of every value.  2^16 <= n <= 2^19,
+ * fused kernel, one read and one write of every value.  2^16 <= n <= 2^22,
  * real to complex: the complex plan's column pass, then its row pass with the
  * split folded in (rows k1 and n/2/N1 - k1 in one tile), two passes.
  * 2^16 <= n <= 2^21, complex to real: the split folded into the complex

@@ -123,7 +123,7 @@ cudaError_t launch_gen_twiddles_n64(double2* tab, long long N, long long count, 
 cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false);
 cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);
 // Real-to-complex transforms of N = 2M reals, M a two-pass four-step length
-// with rows of 2^6..2^10 points: the even/odd split folded into the row pass
+// with rows of 2^6..2^12 points: the even/odd split folded into the row pass
 // (real_fold.cu).
 struct TileKernelInfo;
 const TileKernelInfo* r2c_fold_kernel_info(int lg2);

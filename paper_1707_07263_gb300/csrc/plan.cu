@@ -1181,7 +1181,7 @@ static int plan_real(fft_plan* p, int lgN) {
   p->inner = create_1d(M, p->batch, FFT_FORWARD, FFT_PREC_FP32, nullptr);
   if (!p->inner) return fft_last_error();
   p->launches = p->inner->launches + 1;
-  // Two-pass inner plans with rows of 2^6..2^10 points and at least 16 rows:
+  // Two-pass inner plans with rows of 2^6..2^12 points and at least 16 rows:
   // the real-to-complex split runs inside the row pass (real_fold.cu), two
   // passes over memory instead of three.
   const fft_plan* q = p->inner;

@@ -1,5 +1,5 @@
 // real_fold.cu -- real-data transforms of N = 2M reals with M = N1 * N2 a
-// two-pass four-step length (2^15..2^18): the even/odd split folded into the
+// two-pass four-step length (2^15..2^21): the even/odd split folded into the
 // row pass of the complex transform (real to complex) or into its column pass
 // (complex to real), so that the transform takes two passes over memory
 // instead of three.
@@ -11,13 +11,14 @@
 // Z[k1 + N1 k2].  The split then needs Z[k] and Z[M - k] together:
 //     X[k] = E + W_N^k O,  E = (Z[k] + conj Z[M-k]) / 2,  O = (Z[k] - conj Z[M-k]) / (2i),
 // and M - k = (N1 - k1) + N1 (N2 - 1 - k2) lies in row N1 - k1 (row 0 and row
-// N1/2 are their own mirrors).  A tile of this kernel therefore takes H = 8
-// mirror pairs of rows -- rows u, u+1, ... and N1 - u, N1 - u - 1, ..., with
-// rows 0 and N1/2 as the pair of u = 0 -- runs their 16 row FFTs with the same
-// Stockham passes as the row pass (tile_fft.cuh, last pass left in shared
-// memory, transposed so that a warp reads 16 rows at one k2 without bank
-// conflicts), and computes every X[k] of those rows from shared memory,
-// stored as 64-byte runs of consecutive k1.  X[M] comes from Z[0].
+// N1/2 are their own mirrors).  A tile of this kernel therefore takes H
+// mirror pairs of rows (8 for rows of up to 2^10 points, 4 for 2^11, 2 for
+// 2^12) -- rows u, u+1, ... and N1 - u, N1 - u - 1, ..., with rows 0 and N1/2
+// as the pair of u = 0 -- runs their 2H row FFTs with the same Stockham
+// passes as the row pass (tile_fft.cuh, last pass left in shared memory,
+// transposed so that a warp reads 2H rows at one k2 without bank conflicts),
+// and computes every X[k] of those rows from shared memory, stored as runs of
+// H consecutive k1 (8 bytes each).  X[M] comes from Z[0].
 #include <cuda_runtime.h>
 
 #include "gbfft_internal.h"
@@ -26,13 +27,16 @@
 
 namespace gbfft {
 
-constexpr int kFoldPairs = 8;               // H: mirror pairs of rows per tile
-constexpr int kFoldCols = 2 * kFoldPairs;   // rows (transform columns) per tile
+constexpr int kFoldCols = 16;   // complex-to-real fold: columns per tile of the inner column pass
+
+// Mirror pairs of rows per tile: 8 for rows of 2^6..2^10 points, fewer for
+// longer rows so that the tile fits shared memory (rows of 2^11: 4, 2^12: 2).
+constexpr int fold_pairs(int lg2) { return lg2 <= 10 ? 8 : (lg2 == 11 ? 4 : 2); }
 
 struct RFoldArgs {
   long long M;             // complex length (N / 2)
   int N1;                  // rows of the four-step view (power of two >= 16)
-  int tiles_per_row;       // N1 / 16
+  int tiles_per_row;       // N1 / (2H)
   const float2* r_lo;      // W_N^k = r_lo[k & (2^r_s - 1)] * r_hi[k >> r_s], k < M
   const float2* r_hi;
   int r_s;
@@ -41,10 +45,18 @@ struct RFoldArgs {
 };
 
 template <int LG2>
-__global__ void __launch_bounds__(TileCfg<LG2, kFoldCols, false, false>::T)
-    r2c_fold_kernel(const TileArgs ta, const RFoldArgs f) {
-  using Cfg = TileCfg<LG2, kFoldCols, false, false>;
-  constexpr int N2 = 1 << LG2, H = kFoldPairs, C = kFoldCols, T = Cfg::T;
+struct FoldCfg {
+  static constexpr int H = fold_pairs(LG2), C = 2 * H;
+  using Tile = TileCfg<LG2, C, false, false>;
+  static constexpr int T = Tile::T;
+  // the exchange tile, or the transposed rows left by the last pass if larger
+  static constexpr int SMEM = cmax(Tile::SMEM_BYTES, (1 << LG2) * (C + 1) * 8);
+};
+
+template <int LG2>
+__global__ void __launch_bounds__(FoldCfg<LG2>::T) r2c_fold_kernel(const TileArgs ta, const RFoldArgs f) {
+  using Cfg = FoldCfg<LG2>;
+  constexpr int N2 = 1 << LG2, H = Cfg::H, C = Cfg::C, T = Cfg::T;
   extern __shared__ float2 smem[];
   __shared__ long long s_off[C];
   __shared__ int s_k1[C];
@@ -61,10 +73,10 @@ __global__ void __launch_bounds__(TileCfg<LG2, kFoldCols, false, false>::T)
   TileArgs a = ta;
   a.col_off = s_off;
   a.ncols = C;
-  float2 v[Cfg::P];
+  float2 v[Cfg::Tile::P];
   tile_stage<LG2, C, false, false, 0, true, 0, 6>(v, smem, a, ta.in + b * ta.in_bstride, nullptr, 0, b, nullptr);
 
-  // every Z of the 16 rows is in shared memory, Z_c[k2] at k2 * (C + 1) + c
+  // every Z of the C rows is in shared memory, Z_c[k2] at k2 * (C + 1) + c
   float2* xr = ta.out + b * (f.M + 1);
   const unsigned lo_mask = (1u << f.r_s) - 1u;
   for (int idx = threadIdx.x; idx < C * N2; idx += T) {
@@ -94,13 +106,13 @@ __global__ void __launch_bounds__(TileCfg<LG2, kFoldCols, false, false>::T)
 }
 
 #define GBFFT_FOLD(LG) \
-  {(const void*)&r2c_fold_kernel<LG>, TileCfg<LG, kFoldCols, false, false>::T, \
-   TileCfg<LG, kFoldCols, false, false>::SMEM_BYTES, LG, kFoldCols, MAP_JJ}
+  {(const void*)&r2c_fold_kernel<LG>, FoldCfg<LG>::T, FoldCfg<LG>::SMEM, LG, FoldCfg<LG>::C, MAP_JJ}
 
-// The fold kernel for rows of 2^lg2 points (2^6..2^10), or NULL.
+// The fold kernel for rows of 2^lg2 points (2^6..2^12), or NULL.
 const TileKernelInfo* r2c_fold_kernel_info(int lg2) {
-  static const TileKernelInfo tab[] = {GBFFT_FOLD(6), GBFFT_FOLD(7), GBFFT_FOLD(8), GBFFT_FOLD(9), GBFFT_FOLD(10)};
-  if (lg2 < 6 || lg2 > 10) return nullptr;
+  static const TileKernelInfo tab[] = {GBFFT_FOLD(6),  GBFFT_FOLD(7),  GBFFT_FOLD(8), GBFFT_FOLD(9),
+                                       GBFFT_FOLD(10), GBFFT_FOLD(11), GBFFT_FOLD(12)};
+  if (lg2 < 6 || lg2 > 12) return nullptr;
   return &tab[lg2 - 6];
 }
 
@@ -134,7 +146,7 @@ int r2c_fold_launch(const TileKernelInfo* k, const TileArgs& a, long long M, int
   RFoldArgs f;
   f.M = M;
   f.N1 = N1;
-  f.tiles_per_row = N1 / kFoldCols;
+  f.tiles_per_row = N1 / k->C;
   f.r_lo = r_lo;
   f.r_hi = r_hi;
   f.r_s = r_s;

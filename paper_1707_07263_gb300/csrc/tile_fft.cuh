@@ -261,7 +261,8 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 //        real-to-complex pairs of the same row; 6: last pass leaves output k
 //        of column c in shared memory at k * (C + 1) + c (transposed: lanes of
 //        consecutive k write, and lanes of consecutive c read, without bank
-//        conflicts) and stops there (the caller combines rows); 4: as 0, and
+//        conflicts) and stops there (the caller combines rows; `sm` must hold
+//        L * (C + 1) entries); 4: as 0, and
 //        once every thread has read its inputs from `sm`, one thread starts
 //        the bulk copy of the next tile's rows (source `gin`, none if NULL)
 //        into `sm`, completing on the mbarrier stored just past the tile.
@@ -433,7 +434,8 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   // ---- scatter outputs ----
   if constexpr (LAST && POST == 6) {
     static_assert(NB == 1 && IDX == 0 && !OUT_CF && !REV, "rows left in shared memory: contiguous rows");
-    static_assert(L * (C + 1) <= C * LP, "transposed rows fit the exchange buffer");
+    // (the caller provides at least L * (C + 1) entries at sm: for C >= 16
+    // the exchange tile itself, otherwise a larger allocation)
     __syncthreads();   // all reads of this pass are done
     float2* wp = sm + jj[0] * (C + 1) + cc[0];
 #pragma unroll

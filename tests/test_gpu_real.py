@@ -43,7 +43,8 @@ def batch_for(n):
     return min(3 * jj_cols(lgm) + 1, max(2, (1 << 17) // n)) if lgm <= 14 else max(1, (1 << 21) // n)
 
 
-@pytest.mark.parametrize("lg", list(range(2, 16)) + [16, 17, 20])
+# 2^16..2^22: the split folded into the row pass of the complex plan
+@pytest.mark.parametrize("lg", list(range(2, 16)) + [16, 17, 19, 20, 21, 22])
 def test_rfft_matches_oracle(lg):
     n = 1 << lg
     batch = batch_for(n)
@@ -79,7 +80,8 @@ def test_round_trip(lg):
 
 @pytest.mark.parametrize("lg", [22, 24])
 def test_large_sampled(lg):
-    """Long rows: the complex plan plus the split kernel; whole rows checked."""
+    """Long rows (2^22: both splits folded; 2^24: the complex plan plus a split
+    kernel); whole rows checked."""
     n = 1 << lg
     x = real_rows(n, 2, seed=6300 + lg)
     got = gb.rfft(torch.from_numpy(x).cuda()).cpu().numpy()
@@ -143,7 +145,7 @@ def test_irfft_gradient_finite_differences():
     assert oracle.rel_l2(Xt.grad.cpu().numpy(), fd) <= 1e-5
 
 
-@pytest.mark.parametrize("lg", [2, 3, 5, 8, 11, 12, 15, 16, 18, 21])
+@pytest.mark.parametrize("lg", [2, 3, 5, 8, 11, 12, 15, 16, 18, 20, 21, 22])
 def test_real_adjoints_match_oracle(lg):
     """The adjoints of the real transforms (FFT_ADJOINT and FFT_INVERSE |
     FFT_ADJOINT on a real plan) against their definitions written with the
