@@ -120,8 +120,12 @@ GBFFT_API fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec)
  * that is not a power of two, FFT_ERR_UNSUPPORTED. */
 GBFFT_API fft_plan* fft_plan_create_2d(int64_t ny, int64_t nx, int64_t batch, int dir, int prec);
 
-/* Plan for `batch` real-data transforms of length n (power of two,
- * 4 <= n <= 2^28; FP32 only, prec must be FFT_PREC_FP32).  Run it with
+/* Plan for `batch` real-data transforms of length n: FFT_PREC_FP32 with n a
+ * power of two, 4 <= n <= 2^28 (float32 rows, complex64 spectra), or
+ * FFT_PREC_FP64 with n even, n >= 4 and n/2 a 7-smooth FP64 length (float64
+ * rows, complex128 spectra, 16-byte aligned; the complex128 plan of length
+ * n/2 plus FP64 split kernels).  Other precisions: FFT_ERR_INVALID_ARG for
+ * lengths that are not powers of two, else FFT_ERR_UNSUPPORTED.  Run it with
  * fft_exec_dir:
  *   FFT_FORWARD (real to complex): in = batch rows of n floats, out = batch
  *     rows of n/2 + 1 complex64 values X[k] = Eq. 1 of the row, k = 0..n/2

@@ -348,20 +348,21 @@ def range_compress(x: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
 
 def _run_real(x: torch.Tensor, n: int, dir: int) -> torch.Tensor:
     """Through a cached real plan: real-to-complex (dir FORWARD, float32 rows
-    of n -> complex64 rows of n/2 + 1) or complex-to-real (dir INVERSE), and
-    their adjoints (ADJOINT: complex rows -> real rows; INVERSE | ADJOINT:
-    real rows -> complex rows)."""
+    of n -> complex64 rows of n/2 + 1; float64 -> complex128 in FP64) or
+    complex-to-real (dir INVERSE), and their adjoints (ADJOINT: complex rows ->
+    real rows; INVERSE | ADJOINT: real rows -> complex rows)."""
     rows = x.shape[:-1]
     batch = 1
     for d in rows:
         batch *= int(d)
+    fp64 = x.dtype in (torch.float64, torch.complex128)
     if dir in (FORWARD, INVERSE | ADJOINT):
-        out = torch.empty(rows + (n // 2 + 1,), dtype=torch.complex64, device=x.device)
+        out = torch.empty(rows + (n // 2 + 1,), dtype=torch.complex128 if fp64 else torch.complex64, device=x.device)
     else:
-        out = torch.empty(rows + (n,), dtype=torch.float32, device=x.device)
+        out = torch.empty(rows + (n,), dtype=torch.float64 if fp64 else torch.float32, device=x.device)
     if batch == 0:
         return out
-    p = get_plan("r2c", (n,), batch, "fp32", x.device)
+    p = get_plan("r2c", (n,), batch, "fp64" if fp64 else "fp32", x.device)
     p.exec_ptr(x.data_ptr(), out.data_ptr(), dir)
     return out
 
@@ -398,19 +399,21 @@ class _IRFFT(torch.autograd.Function):
 
 
 def rfft(x: torch.Tensor) -> torch.Tensor:
-    """Eq. 1 of real rows (last dimension, length n a power of two >= 4):
-    the n/2 + 1 non-redundant outputs.  x: float32 CUDA tensor; returns
-    complex64.  One fused kernel for n <= 2^15.  Differentiable."""
-    if not isinstance(x, torch.Tensor) or x.dtype != torch.float32 or not x.is_cuda:
-        raise TypeError("expected a float32 CUDA tensor")
+    """Eq. 1 of real rows (last dimension): the n/2 + 1 non-redundant
+    outputs.  float32 CUDA tensor (n a power of two >= 4; one fused kernel for
+    n <= 2^15) -> complex64, or float64 (FP64; any even n >= 4 whose half is
+    a 7-smooth FP64 length) -> complex128.  Differentiable."""
+    if not isinstance(x, torch.Tensor) or x.dtype not in (torch.float32, torch.float64) or not x.is_cuda:
+        raise TypeError("expected a float32 or float64 CUDA tensor")
     return _RFFT.apply(x.contiguous())
 
 
 def irfft(X: torch.Tensor, n: int | None = None) -> torch.Tensor:
     """Eq. 2 (with 1/n) of the Hermitian extension of X[0..n/2] (last
     dimension): real rows of length n (default 2 * (X.shape[-1] - 1)); the
-    imaginary parts of X[0] and X[n/2] are ignored.  Differentiable."""
-    _check_input(X)
+    imaginary parts of X[0] and X[n/2] are ignored.  complex64 -> float32,
+    complex128 -> float64 (FP64).  Differentiable."""
+    _check_input(X, allow_fp64=True)
     if n is None:
         n = 2 * (X.shape[-1] - 1)
     if X.shape[-1] != n // 2 + 1:

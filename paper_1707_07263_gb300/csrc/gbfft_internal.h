@@ -137,6 +137,10 @@ cudaError_t launch_r2c_split(const float2* z, float2* x, long long M, long long 
                              const float2* hi, int s, float s_int, float s_end, cudaStream_t st);
 cudaError_t launch_c2r_split(const float2* x, float2* z, long long M, long long batch, const float2* lo,
                              const float2* hi, int s, float end_mul, cudaStream_t st);
+cudaError_t launch_r2c_split64(const double2* z, double2* x, long long M, long long batch, const double2* lo,
+                               const double2* hi, int s, double s_int, double s_end, cudaStream_t st);
+cudaError_t launch_c2r_split64(const double2* x, double2* z, long long M, long long batch, const double2* lo,
+                               const double2* hi, int s, double end_mul, cudaStream_t st);
 
 }  // namespace gbfft
 

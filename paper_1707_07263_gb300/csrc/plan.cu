@@ -433,9 +433,32 @@ static int exec_filter_plan(fft_plan* p, const float2* in, float2* out, const fl
 int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s);
 
 // ---- real-data transforms (KIND_REAL): N = 2M reals per row ----------------
+// FP64 real-data plans: the complex128 plan and the FP64 split kernels.
+static int exec_real64(fft_plan* p, const void* in, void* out, bool to_complex, bool adj, cudaStream_t s) {
+  const long long M = p->n / 2;
+  if (!p->inner || !p->zbuf) return FFT_ERR_NO_WORKSPACE;
+  const double2* lo = (const double2*)p->r_lo;
+  const double2* hi = (const double2*)p->r_hi;
+  double2* z = (double2*)p->zbuf;
+  if (to_complex) {
+    const int rc = exec_plan(p->inner, in, z, FFT_FORWARD, s);
+    if (rc) return rc;
+    const double s_int = adj ? 1.0 / (double)M : 1.0, s_end = adj ? 0.5 / (double)M : 1.0;
+    return launch_r2c_split64(z, (double2*)out, M, p->batch, lo, hi, p->r_s, s_int, s_end, s) == cudaSuccess
+               ? FFT_OK
+               : FFT_ERR_CUDA;
+  }
+  if (launch_c2r_split64((const double2*)in, z, M, p->batch, lo, hi, p->r_s, adj ? 2.0 : 1.0, s) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  return exec_plan(p->inner, z, out, adj ? FFT_ADJOINT : FFT_INVERSE, s);
+}
+
 static int exec_real(fft_plan* p, const float2* in, float2* out, int dir, cudaStream_t s) {
   if (dir < 0 || dir > (FFT_INVERSE | FFT_ADJOINT)) return FFT_ERR_INVALID_ARG;
   if ((const void*)in == (const void*)out) return FFT_ERR_INVALID_ARG;
+  if (p->prec == FFT_PREC_FP64)
+    return exec_real64(p, in, out, dir == FFT_FORWARD || dir == (FFT_INVERSE | FFT_ADJOINT),
+                       (dir & FFT_ADJOINT) != 0, s);
   const long long M = p->n / 2;
   // Real rows in, complex rows out: the transform (FFT_FORWARD) and the adjoint
   // of the complex-to-real transform (FFT_INVERSE | FFT_ADJOINT), which is the
@@ -1205,8 +1228,57 @@ static int plan_real(fft_plan* p, int lgN) {
   return FFT_OK;
 }
 
+// FP64 real-data plans: N = 2M reals, the complex128 plan of length M (one
+// mixed-radix pass or the strided four-step passes) plus the FP64 split
+// kernels, with a two-level FP64 table W_N^k, k < M.
+static int plan_real64(fft_plan* p) {
+  const long long M = p->n / 2;
+  p->inner = create_1d(M, p->batch, FFT_FORWARD, FFT_PREC_FP64, nullptr);
+  if (!p->inner) return fft_last_error();
+  int bits = 0;
+  while ((1LL << bits) < M) ++bits;
+  p->r_s = (bits + 1) / 2;
+  const long long nlo = 1LL << p->r_s, nhi = ((M - 1) >> p->r_s) + 1;
+  const size_t hi_off = align256((size_t)nlo * 16);
+  if (cudaMalloc(&p->d_rtw, hi_off + (size_t)nhi * 16) != cudaSuccess) return FFT_ERR_ALLOC;
+  p->r_lo = (const float2*)p->d_rtw;   // complex128 entries
+  p->r_hi = (const float2*)((char*)p->d_rtw + hi_off);
+  if (launch_gen_twiddles_step((void*)p->r_lo, true, p->n, nlo, 1, 0) != cudaSuccess ||
+      launch_gen_twiddles_step((void*)p->r_hi, true, p->n, nhi, nlo, 0) != cudaSuccess ||
+      cudaStreamSynchronize(0) != cudaSuccess)
+    return FFT_ERR_CUDA;
+  p->launches = p->inner->launches + 1;
+  p->d_status = p->inner->d_status;
+  p->ws_bytes = align256(p->inner->ws_bytes) + (size_t)M * (size_t)p->batch * 16;
+  return FFT_OK;
+}
+
 fft_plan* fft_plan_create_r2c(int64_t n, int64_t batch, int prec) {
   const int lgN = ilog2_exact(n);
+  if (prec == FFT_PREC_FP64) {
+    // any even n >= 4 whose half is a 7-smooth FP64 length
+    if (n < 4 || (n & 1) || !smooth7(n / 2) || batch < 1 || (double)n * (double)batch > 9.0e15) {
+      set_err(FFT_ERR_INVALID_ARG);
+      return nullptr;
+    }
+    fft_plan* p = new_plan();
+    if (!p) {
+      set_err(FFT_ERR_ALLOC);
+      return nullptr;
+    }
+    p->kind = KIND_REAL;
+    p->n = n;
+    p->batch = batch;
+    p->dir = FFT_FORWARD;
+    p->prec = prec;
+    const int rc = plan_real64(p);
+    if (rc != FFT_OK) {
+      free_plan(p);
+      set_err(rc);
+      return nullptr;
+    }
+    return publish(p);
+  }
   if (lgN < 2 || lgN > FFT_MAX_LOG2N || batch < 1 || !valid_prec(prec) || (double)n * (double)batch > 9.0e15) {
     set_err(FFT_ERR_INVALID_ARG);
     return nullptr;

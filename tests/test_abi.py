@@ -216,8 +216,14 @@ def test_fp64_and_mixed_length_limits(lib):
     arr = (ctypes.c_int64 * 2)(16, 32)
     assert lib.fft_plan_create_many(arr, 2, 0, fp64) is None
     assert lib.fft_last_error() == -6
-    assert lib.fft_plan_create_r2c(16, 1, fp64) is None
+    assert lib.fft_plan_create_r2c(22, 1, fp64) is None          # half length 11
+    assert lib.fft_last_error() == -1
+    assert lib.fft_plan_create_r2c(15, 1, fp64) is None          # odd
+    assert lib.fft_last_error() == -1
+    assert lib.fft_plan_create_r2c(2 * 7168 * 7168 * 2, 1, fp64) is None   # half beyond two FP64 passes
     assert lib.fft_last_error() == -6
+    assert lib.fft_plan_create_r2c(24, 1, 1) is None             # real data on the tensor cores
+    assert lib.fft_last_error() == -1
 
 
 def test_pointers_that_are_not_live_plans(lib):

@@ -111,3 +111,63 @@ def test_limits():
     lib.fft_destroy(h)
     with pytest.raises(ValueError):
         gb.fft(torch.zeros(16, dtype=torch.complex128, device="cuda"), prec="fp32")
+
+
+# ---- FP64 real-data transforms (float64 rows, complex128 spectra) ----------------
+
+def real64(n, batch, seed):
+    return np.random.Generator(np.random.PCG64(seed)).uniform(-1.0, 1.0, (batch, n))
+
+
+def half64(n, batch, seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    return g.normal(0, 1, (batch, n // 2 + 1)) + 1j * g.normal(0, 1, (batch, n // 2 + 1))
+
+
+# one-pass inner lengths (n/2 <= 7168, powers of two and 7-smooth, odd n/2
+# included) and two-pass ones (n/2 > 7168)
+@pytest.mark.parametrize("n", [4, 6, 16, 30, 1024, 2000, 2250, 14336, 1 << 14, 20000, 1 << 20])
+def test_real_fp64_matches_oracle(n):
+    batch = 3 if n <= 1 << 14 else 1
+    x = real64(n, batch, 9400 + n % 997)
+    X = gb.rfft(torch.from_numpy(x).cuda())
+    assert X.dtype == torch.complex128 and X.shape == (batch, n // 2 + 1)
+    Xh = X.cpu().numpy()
+    H = half64(n, batch, 9500 + n % 997)
+    back = gb.irfft(torch.from_numpy(H).cuda(), n)
+    assert back.dtype == torch.float64 and back.shape == (batch, n)
+    if n <= 1 << 14 or (n & (n - 1)) == 0:
+        assert oracle.rel_l2_rows(Xh, oracle.rfft(x)).max() <= tol(n), f"rfft N={n}"
+        assert oracle.rel_l2_rows(back.cpu().numpy(), oracle.irfft(H, n)).max() <= tol(n), f"irfft N={n}"
+    else:
+        ks = np.array([0, 1, 7, n // 4, n // 2 - 1, n // 2])
+        assert oracle.rel_l2_rows(Xh[:, ks], oracle.dft_bins(x.astype(np.complex128), ks)).max() <= tol(n)
+    rt = gb.irfft(X, n).cpu().numpy()
+    assert oracle.rel_l2_rows(rt, x).max() <= 2 * tol(n), f"round trip N={n}"
+
+
+@pytest.mark.parametrize("n", [16, 2000, 1 << 14])
+def test_real_fp64_adjoints_and_gradient(n):
+    """The adjoints of both directions (the gradients of rfft and irfft)
+    against their definitions, through autograd."""
+    x = real64(n, 2, 9600 + n)
+    w = np.random.Generator(np.random.PCG64(9601 + n)).uniform(0, 1, n // 2 + 1)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    X = gb.rfft(xt)
+    (torch.abs(X * torch.from_numpy(w).cuda()) ** 2).sum().backward()
+    # L = sum_k w_k^2 |X_k|^2 over the kept bins: dL/dx_m = Re sum_k 2 w_k^2 X_k W^{-mk} (k <= n/2)
+    Xr = oracle.rfft(x)
+    g = np.zeros((2, n), dtype=np.complex128)
+    g[:, : n // 2 + 1] = 2 * w ** 2 * Xr
+    g_ref = oracle.transform(g, oracle.ADJOINT).real
+    assert oracle.rel_l2(xt.grad.cpu().numpy(), g_ref) <= 4 * tol(n)
+    H = half64(n, 2, 9700 + n)
+    Ht = torch.from_numpy(H).cuda().requires_grad_(True)
+    y = gb.irfft(Ht, n)
+    v = real64(n, 2, 9701 + n)
+    (y * torch.from_numpy(v).cuda()).sum().backward()
+    # d/dH of sum v * irfft(H): Eq. 1 of v with bins 1..n/2-1 times 2/n and bins 0, n/2 times 1/n
+    V = oracle.rfft(v)
+    scale = np.full(n // 2 + 1, 2.0 / n)
+    scale[0] = scale[-1] = 1.0 / n
+    assert oracle.rel_l2(Ht.grad.cpu().numpy(), V * scale) <= 4 * tol(n)
