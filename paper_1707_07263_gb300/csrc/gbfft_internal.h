@@ -25,6 +25,7 @@ struct PassDesc {
   long long ntiles;
   const TileKernelInfo* kcol;  // tensor-TMA variant of a column pass (or NULL)
   int col_grid;                // its resident-CTA grid
+  const TileKernelInfo* kst;   // row pass with a tensor-TMA output store (or NULL)
 };
 constexpr int kMaxPasses = 4;
 

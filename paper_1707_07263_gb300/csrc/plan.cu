@@ -312,6 +312,20 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
 // column pass at every multi-pass length (autotuner: 2^16 395 -> 328 us,
 // 2^20 499 -> 427, 2^24 639 -> 514, 2^26 690 -> 580 per 2^26 points).
 // Whether a given exec can use it (alignment, strides) is decided per call.
+// The last pass of a multi-pass 1-D plan, when it is a row pass with a
+// TMA-store variant (row_tmas.cu).
+static int attach_rowtmas(fft_plan* p) {
+  if (env_int("GBFFT_ROWTMAS", 1) == 0) return FFT_OK;
+  PassDesc& d = p->pass[p->npass - 1];
+  if (!d.k || d.k->map != MAP_JC) return FFT_OK;
+  const TileKernelInfo* k = tile_kernel_rowtmas(d.k->lg, d.k->C);
+  if (!k) return FFT_OK;
+  const int rc = prepare_kernel(k);
+  if (rc) return rc;
+  d.kst = k;
+  return FFT_OK;
+}
+
 static int attach_coltma(fft_plan* p, bool want) {
   const int env = env_int("GBFFT_COLTMA", -1);
   if (env >= 0) want = env > 0;
@@ -348,9 +362,13 @@ static int exec_passes(fft_plan* p, const float2* in, float2* out, int dir, cuda
     a.out = roles[d.out_role];
     if (i == 0) a.conj_in = x.conj;
     if (i == p->npass - 1) set_out_xf(a, x);
-    const int rc = (d.kcol && coltma_usable(d.kcol, a, a.in))
-                       ? coltma_launch(d.kcol, a, d.ntiles, d.col_grid, p->d_status, s)
-                       : launch_tile(d.k, a, d.ntiles, s);
+    int rc;
+    if (d.kcol && coltma_usable(d.kcol, a, a.in))
+      rc = coltma_launch(d.kcol, a, d.ntiles, d.col_grid, p->d_status, s);
+    else if (d.kst && rowtmas_usable(d.kst, a, a.out, d.ntiles))
+      rc = rowtmas_launch(d.kst, a, d.ntiles, s);
+    else
+      rc = launch_tile(d.k, a, d.ntiles, s);
     if (rc) return rc;
   }
   return FFT_OK;
@@ -550,6 +568,7 @@ static int exec_real(fft_plan* p, const float2* in, float2* out, int dir, cudaSt
     b.scale_out = 1;
     b.sx = adj ? 1.0f : (float)(1.0 / (double)M);
     b.sy = -b.sx;
+    if (B.kst && rowtmas_usable(B.kst, b, b.out, B.ntiles)) return rowtmas_launch(B.kst, b, B.ntiles, s);
     return launch_tile(B.k, b, B.ntiles, s);
   }
   if (to_complex) {
@@ -817,7 +836,9 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     p->npass = 2;
     p->launches = 2;
     p->ws_bytes = (size_t)p->n * (size_t)p->batch * 8;
-    return attach_coltma(p, cfg->tma > 0 || (cfg->tma < 0 && p->prec == FFT_PREC_FP32));
+    int rc2 = attach_coltma(p, cfg->tma > 0 || (cfg->tma < 0 && p->prec == FFT_PREC_FP32));
+    if (!rc2 && p->prec == FFT_PREC_FP32) rc2 = attach_rowtmas(p);
+    return rc2;
   }
   // three passes, N = N1 * N2 * N3 (M = N2 * N3):
   //   A  columns of length N1 over stride M, scaled by W_N^{m*k1}     in -> ws

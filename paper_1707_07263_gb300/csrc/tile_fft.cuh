@@ -262,7 +262,9 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 //        of column c in shared memory at k * (C + 1) + c (transposed: lanes of
 //        consecutive k write, and lanes of consecutive c read, without bank
 //        conflicts) and stops there (the caller combines rows; `sm` must hold
-//        L * (C + 1) entries); 4: as 0, and
+//        L * (C + 1) entries); 7: last pass of a row pass (j-fast in, c-fast
+//        out) leaves its scaled outputs as a dense tile sm[k * C + c] for a
+//        tensor-TMA store by the caller; 4: as 0, and
 //        once every thread has read its inputs from `sm`, one thread starts
 //        the bulk copy of the next tile's rows (source `gin`, none if NULL)
 //        into `sm`, completing on the mbarrier stored just past the tile.
@@ -432,7 +434,21 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
   for (int i = 0; i < NB; ++i) dft_fwd<R>(v + i * R);
 
   // ---- scatter outputs ----
-  if constexpr (LAST && POST == 6) {
+  if constexpr (LAST && POST == 7) {
+    static_assert(NB == 1 && IDX == 0 && OUT_CF && !IN_CF && !REV && !OFFS, "row pass: outputs to a dense tile");
+    // the scaled outputs of the C rows as a dense [k][c] tile at sm (C * L
+    // entries, inside the exchange tile): adjacent lanes (adjacent c, or the
+    // next k) write adjacent words; the caller stores the tile with tensor TMA
+    __syncthreads();   // all reads of this pass are done
+    if (a.scale_out) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) v[q] = make_float2(v[q].x * a.sx, v[q].y * a.sy);
+    }
+    float2* wp = sm + jj[0] * C + cc[0];
+#pragma unroll
+    for (int q = 0; q < R; ++q) wp[q * NS * C] = v[q];
+    __syncthreads();
+  } else if constexpr (LAST && POST == 6) {
     static_assert(NB == 1 && IDX == 0 && !OUT_CF && !REV, "rows left in shared memory: contiguous rows");
     // (the caller provides at least L * (C + 1) entries at sm: for C >= 16
     // the exchange tile itself, otherwise a larger allocation)
@@ -593,7 +609,7 @@ __device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT
 // One tile of a pass: tile index `tile` of the launch described by `a`, using
 // `smem` (TileCfg::SMEM_BYTES).  Shared by the one-tile-per-CTA kernel below
 // and the persistent uneven-batch kernel.
-template <int LG, int C, bool IN_CF, bool OUT_CF, bool OFFS = false, int PRE = 0>
+template <int LG, int C, bool IN_CF, bool OUT_CF, bool OFFS = false, int PRE = 0, int POST = 0>
 __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, float2* smem) {
   using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
   float2* sm = smem;
@@ -625,7 +641,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, flo
   }
 
   float2 v[Cfg::P];
-  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS, PRE>(v, sm, a, gin, gout, col0, b, epi_tab);
+  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS, PRE, POST>(v, sm, a, gin, gout, col0, b, epi_tab);
 }
 
 // Two CTAs per transform of length 2^(LG+1) (radix-2 decimation in

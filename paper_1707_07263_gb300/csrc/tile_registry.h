@@ -33,6 +33,13 @@ bool coltma_usable(const TileKernelInfo* k, const TileArgs& a, const void* in);
 int coltma_launch(const TileKernelInfo* k, const TileArgs& a, long long ntiles, int grid, int* status,
                   cudaStream_t s);
 
+// Row-pass kernels (MAP_JC) whose output tile is written by tensor TMA
+// (row_tmas.cu), rows of 2^10 and 2^11 points, four per CTA; signature
+// void(CUtensorMap, TileArgs).
+const TileKernelInfo* tile_kernel_rowtmas(int lg, int C);
+bool rowtmas_usable(const TileKernelInfo* k, const TileArgs& a, const void* out, long long ntiles);
+int rowtmas_launch(const TileKernelInfo* k, const TileArgs& a, long long ntiles, cudaStream_t s);
+
 // Two-CTA radix-2 split kernels (tile_fft_dif2_kernel) for half length 2^lg.
 const TileKernelInfo* tile_kernel_dif2(int lg);
 

@@ -216,6 +216,26 @@ def test_two_pass_forced_at_2_24(hooks_lib, monkeypatch):
     assert_rows(got, oracle.fft(x.astype(np.complex128)), tol32(n), "two-pass 2^24")
 
 
+# Row passes of 2^10 / 2^11 points store their output tile with tensor TMA
+# (2^18 = 2^8 x 2^10, 2^19 = 2^8 x 2^11, 2^21 = 2^10 x 2^11): whole 2^26-point
+# launches (every CTA's boxes), rows sampled, both directions, in place, and
+# the plain store path of the test build (GBFFT_ROWTMAS=0) bit-identical.
+@pytest.mark.parametrize("lg", [18, 19, 21])
+def test_tma_store_row_pass_full_size(lib, hooks_lib, monkeypatch, lg):
+    n = 1 << lg
+    batch = (1 << 26) // n
+    x = workloads.cgauss(n, batch, seed=5650 + lg)
+    rows = np.unique(np.concatenate([np.arange(0, batch, max(1, batch // 7)), [batch - 1]]))
+    ref = oracle.fft(x[rows].astype(np.complex128))
+    got = run_1d(lib, x, 0)
+    assert_rows(got[rows], ref, tol32(n), f"TMA-store rows N=2^{lg}")
+    back = run_1d(lib, got, 1, inplace=True)
+    assert_rows(back[rows], x[rows].astype(np.complex128), 2 * tol32(n), f"TMA-store rows inverse N=2^{lg}")
+    monkeypatch.setenv("GBFFT_ROWTMAS", "0")
+    plain = run_1d(hooks_lib, x, 0)
+    assert np.array_equal(plain, got), f"N=2^{lg}: TMA-store and plain row pass differ"
+
+
 # --- full-size large transforms (config 3a) ----------------------------------------
 @pytest.mark.parametrize("lg,batch", [(24, 1), (26, 1), (24, 2)])
 def test_fourstep_full_size(lib, lg, batch):
