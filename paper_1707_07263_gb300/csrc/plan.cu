@@ -772,11 +772,14 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   if (p->prec != FFT_PREC_FP32) npass = 2;  // tensor-core kernels are compiled for two-pass splits
   if (npass == 2 && lgN > 28) return FFT_ERR_UNSUPPORTED;
   if (npass == 2) {
-    // measured on GB300 (autotuner): 2^8-point column tiles of 16 columns win
-    // up to 2^20; beyond, the even split
+    // measured on GB300 (autotuner, per 2^26 points): rows of 2^10 or 2^11
+    // points, whose row pass stores by tensor TMA, from 2^17 (2^7 x 2^10:
+    // 336 us against 375 for 2^8 x 2^9; 2^20 = 2^10 x 2^10: 419 against 436
+    // for 2^8 x 2^12); 2^8 x 2^8 at 2^16; beyond 2^20, the even split
     // (tensor-core plans keep the even split their kernels are compiled for)
     const bool fp32 = p->prec == FFT_PREC_FP32;
-    int lg2 = (fp32 && lgN >= 16 && lgN <= 20) ? lgN - 8 : (lgN + 1) / 2;
+    static const int kLg2Default[5] = {8, 10, 10, 11, 10};   // lgN = 16..20
+    int lg2 = (fp32 && lgN >= 16 && lgN <= 20) ? kLg2Default[lgN - 16] : (lgN + 1) / 2;
     const int force_lg1 = cfg->lg1 > 0 ? cfg->lg1 : env_int("GBFFT_FORCE_SPLIT", 0);
     if (force_lg1 > 0 && force_lg1 < lgN && lgN - force_lg1 <= 14 && force_lg1 <= 14) lg2 = lgN - force_lg1;
     const int lg1 = lgN - lg2;

@@ -27,8 +27,6 @@
 
 namespace gbfft {
 
-constexpr int kFoldCols = 16;   // complex-to-real fold: columns per tile of the inner column pass
-
 // Mirror pairs of rows per tile: 8 for rows of 2^6..2^10 points, fewer for
 // longer rows so that the tile fits shared memory (rows of 2^11: 4, 2^12: 2).
 constexpr int fold_pairs(int lg2) { return lg2 <= 10 ? 8 : (lg2 == 11 ? 4 : 2); }
@@ -123,21 +121,23 @@ const TileKernelInfo* r2c_fold_kernel_info(int lg2) {
 // N2 - n2 of the same transform, usually an L2 hit.  The column pass then
 // continues as the complex plan's own (four-step twiddle, workspace), and the
 // row pass is the complex plan's.
-template <int LG1>
-__global__ void __launch_bounds__(TileCfg<LG1, kFoldCols, true, true>::T) c2r_fold_kernel(const TileArgs a) {
+template <int LG1, int C>
+__global__ void __launch_bounds__(TileCfg<LG1, C, true, true>::T) c2r_fold_kernel(const TileArgs a) {
   extern __shared__ float2 smem[];
-  tile_body<LG1, kFoldCols, true, true, false, 7>(a, (long long)blockIdx.x, smem);
+  tile_body<LG1, C, true, true, false, 7>(a, (long long)blockIdx.x, smem);
 }
 
-#define GBFFT_CFOLD(LG) \
-  {(const void*)&c2r_fold_kernel<LG>, TileCfg<LG, kFoldCols, true, true>::T, \
-   TileCfg<LG, kFoldCols, true, true>::SMEM_BYTES, LG, kFoldCols, MAP_CC}
+#define GBFFT_CFOLD(LG, C) \
+  {(const void*)&c2r_fold_kernel<LG, C>, TileCfg<LG, C, true, true>::T, TileCfg<LG, C, true, true>::SMEM_BYTES, LG, \
+   C, MAP_CC}
 
-// The folded column kernel for columns of 2^lg1 points, C per CTA, or NULL.
+// The folded column kernel for columns of 2^lg1 points, C per CTA (the inner
+// plans' column tiles: 2^7 and 2^8 with 16 columns, 2^10 with 8), or NULL.
 const TileKernelInfo* c2r_fold_kernel_info(int lg1, int C) {
-  static const TileKernelInfo tab[] = {GBFFT_CFOLD(7), GBFFT_CFOLD(8)};
-  if (C != kFoldCols || lg1 < 7 || lg1 > 8) return nullptr;
-  return &tab[lg1 - 7];
+  static const TileKernelInfo tab[] = {GBFFT_CFOLD(7, 16), GBFFT_CFOLD(8, 16), GBFFT_CFOLD(10, 8)};
+  for (const TileKernelInfo& k : tab)
+    if (k.lg == lg1 && k.C == C) return &k;
+  return nullptr;
 }
 
 int r2c_fold_launch(const TileKernelInfo* k, const TileArgs& a, long long M, int N1, long long batch,
