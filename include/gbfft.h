@@ -111,7 +111,11 @@ GBFFT_API fft_plan* fft_plan_create(int64_t n, int64_t batch, int dir, int prec)
 /* Plan for `batch` 2-D transforms of ny-by-nx row-major images: 1-D
  * transforms of every row, then of every column (Sec. 2.3.2: rows, then
  * columns).  Power-of-two sides 2 <= ny, nx <= 2^14 run on the radix-16 tile
- * kernels (every precision but FP64).  Sides that are 7-smooth but not both
+ * kernels (every precision but FP64): a row pass and one or two column
+ * passes, or, for sides of 2^10..2^12 (ny >= 2^11, or 1024 x 1024), two row
+ * passes that each store their result transposed (the second transforms the
+ * columns as rows); a workspace of one image batch where fft_plan_workspace_bytes
+ * says so.  Sides that are 7-smooth but not both
  * powers of two (FP32, up to 14336), and every FP64 plan (7-smooth sides up
  * to 7168), run as a row pass and a column pass of the strided mixed-radix
  * kernel, the column pass in place in the output (no workspace; fft_plan_kind

@@ -317,7 +317,7 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
 static int attach_rowtmas(fft_plan* p) {
   if (env_int("GBFFT_ROWTMAS", 1) == 0) return FFT_OK;
   PassDesc& d = p->pass[p->npass - 1];
-  if (!d.k || d.k->map != MAP_JC) return FFT_OK;
+  if (!d.k || d.k->map != MAP_JC || d.k->lg > 11) return FFT_OK;
   const TileKernelInfo* k = tile_kernel_rowtmas(d.k->lg, d.k->C);
   if (!k) return FFT_OK;
   const int rc = prepare_kernel(k);
@@ -947,7 +947,93 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
 // columns (>= 64 contiguous bytes per row); taller images split the column
 // length ny = Y1*Y2 into two column passes (the four-step split applied along
 // y), so every column tile stays 16 columns wide.
+// 2-D in two passes over memory, each a row transform whose output is stored
+// transposed (rows of the image in, columns of the result out): pass 1 takes
+// the rows of x (length nx) to ws[b][kx][y], pass 2 the rows of ws (length
+// ny) to out[b][ky][kx].  The column transforms thus read contiguous rows;
+// the transposition is in the stores (runs of C adjacent outputs, C rows per
+// CTA).
+static int build_2d_transposed(fft_plan* p, int ly, int lx) {
+  const long long ny = p->ny, nx = p->nx, img = ny * nx;
+  // rows per CTA: as many as a 2^14-point tile holds, at most 8 (longer output runs)
+  auto pick = [](int lg, long long rows) {
+    int c = (int)std::min<long long>(std::min(16384 >> lg, 8), rows);
+    while (c > 1 && !tile_kernel(MAP_JC, lg, c)) c >>= 1;
+    return c;
+  };
+  const int c1 = pick(lx, ny), c2 = pick(ly, nx);
+  const TileKernelInfo* k1 = tile_kernel(MAP_JC, lx, c1);
+  const TileKernelInfo* k2 = tile_kernel(MAP_JC, ly, c2);
+  if (!k1 || !k2 || ny % c1 || nx % c2) return FFT_ERR_UNSUPPORTED;
+  int rc = prepare_kernel(k1);
+  if (!rc) rc = prepare_kernel(k2);
+  const int lgs[3] = {lx, ly, 0};
+  const int lgNs[2] = {0, 0};
+  if (!rc) rc = build_tables_multi(p, lgs, lgNs);
+  if (rc) return rc;
+  PassDesc& A = p->pass[0];
+  A.k = k1;
+  base_args(A.a);
+  A.a.tw = p->tw1;
+  A.a.tiles_per_batch = ny / c1;
+  A.a.in_bstride = A.a.out_bstride = img;
+  A.a.in_gstride = (long long)c1 * nx;
+  A.a.in_sc = nx;
+  A.a.in_sn = 1;
+  A.a.out_gstride = c1;
+  A.a.out_sc = 1;
+  A.a.out_sn = ny;
+  A.a.ncols = ny;
+  A.a.stream_out = 0;  // read back by pass 2
+  A.in_role = 0;
+  A.out_role = 2;
+  A.ntiles = A.a.tiles_per_batch * p->batch;
+  PassDesc& B = p->pass[1];
+  B.k = k2;
+  base_args(B.a);
+  B.a.tw = p->tw2;
+  B.a.tiles_per_batch = nx / c2;
+  B.a.in_bstride = B.a.out_bstride = img;
+  B.a.in_gstride = (long long)c2 * ny;
+  B.a.in_sc = ny;
+  B.a.in_sn = 1;
+  B.a.out_gstride = c2;
+  B.a.out_sc = 1;
+  B.a.out_sn = nx;
+  B.a.ncols = nx;
+  B.a.stream_in = 0;
+  B.in_role = 2;
+  B.out_role = 1;
+  B.ntiles = B.a.tiles_per_batch * p->batch;
+  p->k1 = k1;
+  p->c1 = c1;
+  p->k2 = k2;
+  p->c2 = c2;
+  p->npass = 2;
+  p->launches = 2;
+  p->ws_bytes = (size_t)img * (size_t)p->batch * 8;
+  for (int i = 0; i < 2 && env_int("GBFFT_ROWTMAS", 1); ++i) {
+    const TileKernelInfo* kt = tile_kernel_rowtmas(p->pass[i].k->lg, p->pass[i].k->C);
+    if (kt) {
+      rc = prepare_kernel(kt);
+      if (rc) return rc;
+      p->pass[i].kst = kt;
+    }
+  }
+  return FFT_OK;
+}
+
 static int build_2d(fft_plan* p, int ly, int lx) {
+  // measured on GB300 per 2^26 points against rows + column passes: 1024^2
+  // 427 -> 388 us, 2048^2 577 -> 507, 4096^2 579 -> 545, 2048 x 1024 578 ->
+  // 443, 4096 x 1024 579 -> 460 (ny x nx); but 1024 x 4096 418 -> 466 (its
+  // rows + one column pass is already two passes) and 8192^2 623 -> 1066 (two
+  // rows per CTA, 16-byte runs), so sides of 2^10..2^12 with ny >= 2^11 or
+  // nx == ny == 2^10
+  const int tr = env_int("GBFFT_2D_TRANSPOSE", -1);
+  const bool transposed = tr >= 0 ? (tr > 0 && lx >= 8 && ly >= 8)
+                                  : (lx >= 10 && lx <= 12 && ly >= 10 && ly <= 12 && (ly >= 11 || lx == 10));
+  if (transposed) return build_2d_transposed(p, ly, lx);
   const long long ny = p->ny, nx = p->nx, img = ny * nx;
   const TileKernelInfo* kr = tile_kernel(MAP_JJ, lx, jj_cols(lx));
   if (!kr) return FFT_ERR_UNSUPPORTED;

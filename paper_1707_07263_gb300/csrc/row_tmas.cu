@@ -56,14 +56,17 @@ __global__ void __launch_bounds__(TileCfg<LG, C, false, true>::T)
   {(const void*)&row_tmas_kernel<LG, C>, TileCfg<LG, C, false, true>::T, TileCfg<LG, C, false, true>::SMEM_BYTES, \
    LG, C, MAP_JC}
 
-// Rows of 2^10 and 2^11 points, four per CTA (256 / 512 threads), where
-// the plain store path is queue-bound.  Measured per 2^26 points against it:
-// 2^18 = 2^8 x 2^10 373.8 -> 335.5 us, 2^19 398.0 -> 365.2, 2^21 = 2^10 x 2^11
-// 482.0 -> 449.2.  Not compiled where it did not pay: rows of 2^12 (one
-// 1024-thread CTA per SM idles while its stores drain: 2^20 435.9 -> 442.0 us)
-// and the 16-row tiles of 2^8 / 2^9 (64- and 128-byte runs, no change).
+// Rows of 2^10 and 2^11 points, four per CTA (256 / 512 threads), and of
+// 2^10 with eight (512 threads), where the plain store path is queue-bound.
+// Measured per 2^26 points against it: 2^18 = 2^8 x 2^10 373.8 -> 335.5 us,
+// 2^19 398.0 -> 365.2, 2^21 = 2^10 x 2^11 482.0 -> 449.2, the transposed 2-D
+// 1024 x 1024 plan 411 -> 388.  Not compiled where it did not pay: every
+// 1024-thread tile (rows of 2^11 with eight, 2^12 with four, 2^13 with two:
+// one CTA per SM idles while its stores drain; 2^20 as 2^8 x 2^12 435.9 ->
+// 442.0 us, 2048^2 506 -> 536, 4096^2 543 -> 564) and the 16-row tiles of 2^8
+// / 2^9 (64- and 128-byte runs, no change).
 const TileKernelInfo* tile_kernel_rowtmas(int lg, int C) {
-  static const TileKernelInfo tab[] = {GBFFT_ROWTMAS(10, 4), GBFFT_ROWTMAS(11, 4)};
+  static const TileKernelInfo tab[] = {GBFFT_ROWTMAS(10, 4), GBFFT_ROWTMAS(11, 4), GBFFT_ROWTMAS(10, 8)};
   for (const TileKernelInfo& k : tab)
     if (k.lg == lg && k.C == C) return &k;
   return nullptr;

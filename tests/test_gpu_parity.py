@@ -287,9 +287,11 @@ def run_2d(lib, x: np.ndarray, d: int) -> np.ndarray:
     return out.cpu().numpy()
 
 
+# (sides of 2^10..2^12 on both axes: the transposed two-pass plan)
 @pytest.mark.parametrize("ny,nx,batch", [(2, 2, 1), (8, 32, 2), (64, 16, 1), (256, 512, 1), (32, 4096, 1),
                                          (4096, 64, 1), (1024, 1024, 1), (2048, 16, 3), (16384, 8, 1),
-                                         (8192, 2, 2)])
+                                         (8192, 2, 2), (1024, 1024, 3), (2048, 1024, 2), (1024, 4096, 1),
+                                         (4096, 4096, 1)])
 @pytest.mark.parametrize("d", ["fwd", "inv"])
 def test_2d(lib, ny, nx, batch, d):
     x = workloads.cgauss(ny * nx, batch, seed=ny * 31 + nx).reshape(batch, ny, nx)
@@ -298,6 +300,31 @@ def test_2d(lib, ny, nx, batch, d):
     tol = tol32(ny * nx)
     for b in range(batch):
         assert oracle.rel_l2(got[b], ref[b]) <= tol, f"2-D {ny}x{nx} {d}"
+
+
+@pytest.mark.parametrize("ny,nx,tr", [(256, 512, "1"), (512, 8192, "1"), (1024, 1024, "0"), (2048, 1024, "0")])
+def test_2d_transposed_switch(hooks_lib, monkeypatch, ny, nx, tr):
+    """The transposed two-pass 2-D plan forced where it is not the default,
+    and the rows + column passes forced where it is (test build)."""
+    monkeypatch.setenv("GBFFT_2D_TRANSPOSE", tr)
+    x = workloads.cgauss(ny * nx, 2, seed=ny + 3 * nx).reshape(2, ny, nx)
+    got = run_2d(hooks_lib, x, 0)
+    ref = oracle.fft2(x.astype(np.complex128))
+    for b in range(2):
+        assert oracle.rel_l2(got[b], ref[b]) <= tol32(ny * nx), f"{ny}x{nx} transposed={tr}"
+
+
+def test_2d_transposed_in_place(lib):
+    ny, nx, batch = 2048, 1024, 3
+    x = workloads.cgauss(ny * nx, batch, seed=91).reshape(batch, ny, nx)
+    p = CPlan(lib, lib.fft_plan_create_2d(ny, nx, batch, 1, 0))
+    xt = torch.from_numpy(x).cuda()
+    out = p.run(xt, 1, out=xt)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = oracle.fft2(x.astype(np.complex128), oracle.INVERSE)
+    for b in range(batch):
+        assert oracle.rel_l2(got[b], ref[b]) <= tol32(ny * nx)
 
 
 def test_2d_one_column_pass_forced(hooks_lib, monkeypatch):
