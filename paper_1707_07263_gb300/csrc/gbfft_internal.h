@@ -26,6 +26,8 @@ struct PassDesc {
   const TileKernelInfo* kcol;  // tensor-TMA variant of a column pass (or NULL)
   int col_grid;                // its resident-CTA grid
   const TileKernelInfo* kst;   // row pass with a tensor-TMA output store (or NULL)
+  const TileKernelInfo* kpfs;  // contiguous one-pass rows: the persistent staged kernel (or NULL)
+  long long pf_grid;           // its resident-CTA grid
 };
 constexpr int kMaxPasses = 4;
 

@@ -363,7 +363,17 @@ static int exec_passes(fft_plan* p, const float2* in, float2* out, int dir, cuda
     if (i == 0) a.conj_in = x.conj;
     if (i == p->npass - 1) set_out_xf(a, x);
     int rc;
-    if (d.kcol && coltma_usable(d.kcol, a, a.in))
+    if (d.kpfs && ((uintptr_t)a.in & 15) == 0) {
+      // contiguous rows, one per CTA in turn; the bulk copies need a 16-byte aligned source
+      long long ntiles = d.ntiles;
+      const long long grid = d.pf_grid < ntiles ? d.pf_grid : ntiles;
+      int* st = p->d_status;
+      void* args[] = {(void*)&a, (void*)&ntiles, (void*)&st};
+      rc = cudaLaunchKernel(d.kpfs->fn, dim3((unsigned)grid), dim3(d.kpfs->threads), args,
+                            (size_t)d.kpfs->smem_bytes, s) == cudaSuccess
+               ? FFT_OK
+               : FFT_ERR_CUDA;
+    } else if (d.kcol && coltma_usable(d.kcol, a, a.in))
       rc = coltma_launch(d.kcol, a, d.ntiles, d.col_grid, p->d_status, s);
     else if (d.kst && rowtmas_usable(d.kst, a, a.out, d.ntiles))
       rc = rowtmas_launch(d.kst, a, d.ntiles, s);
@@ -1055,6 +1065,21 @@ static int build_2d(fft_plan* p, int ly, int lx) {
   R.ntiles = R.a.tiles_per_batch;
   p->k1 = kr;
   p->c1 = Cr;
+  if (Cr == 1 && lx >= 13 && env_int("GBFFT_2D_ROWS_PFS", 1)) {
+    // rows of 2^13 and 2^14 points: the persistent kernel that stages the
+    // next row by a bulk copy, as the 1-D single pass (8192^2: 623 -> 611 us,
+    // 512 x 8192: 464 -> 449; rows of 2^12 measured slower, 416 -> 427)
+    const TileKernelInfo* kp = tile_kernel_pfs(lx);
+    int per_sm = 0, sms = 0, dev = 0;
+    if (kp && !prepare_kernel(kp) && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp->fn, kp->threads, (size_t)kp->smem_bytes) ==
+            cudaSuccess &&
+        per_sm >= 1) {
+      R.kpfs = kp;
+      R.pf_grid = (long long)per_sm * sms;
+    }
+  }
   if (!two) {
     const int C = (int)std::min<long long>(env_int("GBFFT_FORCE_C2", default_cols(ly)), nx);
     const TileKernelInfo* kc = tile_kernel(MAP_CC, ly, C);
