@@ -31,7 +31,7 @@ Also printed on the same JSON line:
 ``--impl reference`` times the oracle instead (the deliberately slow CPU
 baseline) and prints the same line with "impl": "reference".
 Other workloads for measurement only: --workload large | tc | many | range | real | mixed | fp64 |
-passes.
+passes | radix.
 """
 from __future__ import annotations
 
@@ -1169,6 +1169,43 @@ def run_measure(args):
         desc = ("two strided mixed-radix passes (four-step N = N1 N2, or rows then columns): FP64 complex128 "
                 "2^25 points per launch, FP32 ~2^26; errors at sampled outputs (term-by-term oracle sums) or "
                 "whole images; cufft_torch = torch.fft (context)")
+    elif args.workload == "radix":
+        # the autotuner's radix dimension for one on-chip pass: radix-16 / 8 / 4 passes (16 / 8 / 4 points
+        # per thread) on the register path, the planner default, and what fft_autotune picks, 2^26 points
+        for lg in range(5, 15):
+            n = 1 << lg
+            batch = TOTAL // n
+            xh = workloads.cgauss(n, batch, seed=workloads.seed_for(1) + lg)
+            x = torch.from_numpy(xh.reshape(-1)).to(dev)
+            y = torch.empty_like(x)
+            ref = oracle.fft(xh[[0, batch - 1]].astype(np.complex128))
+            row = {"n": n, "batch": batch}
+            cands = [("default", None)] + [(f"radix{r}", {"npass": 1, "tma": 0, "radix": r}) for r in (16, 8, 4)]
+            for name, cfg in cands:
+                if cfg is None:
+                    h = lib.fft_plan_create(n, batch, 0, 0)
+                else:
+                    c = _lib.FftPlanConfig.from_dict(cfg)
+                    h = lib.fft_plan_create_config(n, batch, 0, 0, ctypes.byref(c))
+                if not h:
+                    row[name] = None
+                    continue
+                h = ctypes.c_void_p(h)
+                us = _time_fn(torch, lambda: run_plan(h, x, y), args.steps, args.warmup, stream) * 1e3
+                got = y.view(batch, n)[[0, batch - 1]].cpu().numpy()
+                err = float(oracle.rel_l2_rows(got, ref).max())
+                row[name] = {"us": round(us, 1), "hbm_frac": round(16.0 * n * batch / (us * 1e-6) / 1e9 / peak, 4),
+                             "rel_l2_max": float(f"{err:.3e}")}
+                lib.fft_destroy(h)
+            best = _lib.FftPlanConfig()
+            best_us = ctypes.c_float(0.0)
+            _lib.check(lib.fft_autotune(n, batch, 0, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                        None, 0, sh, args.steps, ctypes.byref(best), ctypes.byref(best_us)))
+            row["autotune"] = {"config": best.as_dict(), "us": round(float(best_us.value), 1)}
+            res.append(row)
+        desc = ("one on-chip pass, N = 2^5..2^14, batch 2^26/N, CN(0,1): register-path kernels with radix-16 / 8 / 4 "
+                "passes (points per thread = radix), the planner default and the autotuner's pick (fft_autotune "
+                "over every candidate, no workspace: single-pass candidates only); sampled rows against the oracle")
     print(json.dumps({"workload": args.workload, "desc": desc, "results": res,
                       "peak_hbm_gbs": peak}), flush=True)
 
@@ -1180,7 +1217,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "large", "tc", "many", "range", "real", "mixed", "fp64",
-                                                          "passes"])
+                                                          "passes", "radix"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

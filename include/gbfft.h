@@ -281,10 +281,17 @@ GBFFT_API int fft_pointer_usable(const void* ptr, size_t bytes);
  * workspace (2^13..2^18; split and columns fixed by the kernel), 0 = one launch
  * per pass.  halves: single pass only, 2 = two CTAs per transform, each
  * computing the even or odd outputs from a radix-2 split of the input
- * (2^12..2^14), <= 1 = one CTA per transform.  These are the knobs of the
- * autotuner (fft_autotune). */
+ * (2^12..2^14), <= 1 = one CTA per transform.  radix: single pass on the
+ * register path only (tma <= 0, halves <= 1, FFT_PREC_FP32): the largest
+ * radix of the Stockham passes, which is also the number of points each
+ * thread holds, and so sets the threads per CTA (transforms per CTA x n /
+ * radix): 8 = radix-8 passes (n = 2^5..2^13), 4 = radix-4 passes
+ * (n = 2^5..2^12), 16 or <= 0 = radix-16 passes (the default; every other
+ * kernel); any other value, or 4 / 8 where no such kernel is compiled, gives
+ * FFT_ERR_UNSUPPORTED.  fft_plan_get_config reports 16 unless a smaller radix
+ * was chosen.  These are the knobs of the autotuner (fft_autotune). */
 typedef struct fft_plan_config {
-  int npass, lg1, lg2, c1, c2, c3, tma, fused, halves;
+  int npass, lg1, lg2, c1, c2, c3, tma, fused, halves, radix;
 } fft_plan_config;
 
 /* As fft_plan_create, with an explicit configuration (NULL = defaults).
@@ -297,7 +304,8 @@ GBFFT_API int fft_plan_get_config(const fft_plan* plan, fft_plan_config* out);
 
 /* Autotuner: builds every candidate configuration for (n, batch, prec) --
  * one or two or three passes, the split lengths near the even split, columns
- * per CTA around the default, TMA staging on/off -- times each with CUDA
+ * per CTA around the default, TMA staging on/off, the largest radix of a
+ * single pass (16, 8 or 4) -- times each with CUDA
  * events over `iters` executions (after 3 untimed ones) on the caller's
  * device buffers in/out (n*batch complex64 each) and workspace ws of ws_bytes
  * (>= n*batch*8 bytes), and writes the fastest configuration to *best and its

@@ -29,7 +29,7 @@ ERRORS = {
 class FftPlanConfig(ctypes.Structure):
     """fft_plan_config of include/gbfft.h."""
     _fields_ = [(name, ctypes.c_int) for name in ("npass", "lg1", "lg2", "c1", "c2", "c3", "tma", "fused",
-                                                  "halves")]
+                                                  "halves", "radix")]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

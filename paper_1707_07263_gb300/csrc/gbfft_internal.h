@@ -123,7 +123,7 @@ int mixed_exec(fft_plan* p, const void* in, void* out, int conj, double sx, doub
 cudaError_t launch_gen_twiddles_n(float2* tab, long long N, long long count, cudaStream_t s);
 cudaError_t launch_gen_twiddles_n64(double2* tab, long long N, long long count, cudaStream_t s);
 
-cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false);
+cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev = false, int lgm = 4);
 cudaError_t launch_gen_power_twiddles(float2* tab, int lgN, long long count, long long step, cudaStream_t s);
 // Real-to-complex transforms of N = 2M reals, M a two-pass four-step length
 // with rows of 2^6..2^12 points: the even/odd split folded into the row pass
@@ -167,6 +167,9 @@ struct fft_plan {
   const gbfft::TileKernelInfo* kpfs;  // its variant staging the next transform by a bulk copy (or NULL;
                                       // kpf is then the fallback for inputs not 16-byte aligned)
   long long pf_grid;                  // its resident-CTA grid
+  const gbfft::TileKernelInfo* kradix;  // single pass with radix-8 / radix-4 passes (config radix), or NULL
+  void* d_radtw;                        // its stage table (schedule of largest radix 2^radix_lgm)
+  int radix_lgm;
   const gbfft::TileKernelInfo* krc;   // fused range-compression kernel of the length (or NULL)
   void* d_rctw;                       // its remainder-last stage table (NULL: the length's own table)
   long long rc_grid;                  // its grid when persistent (0: one tile per CTA)

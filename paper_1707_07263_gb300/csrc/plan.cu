@@ -186,6 +186,7 @@ static void free_plan(fft_plan* p) {
   if (p->ws_owned && p->ws) cudaFree(p->ws);
   if (p->d_tc) cudaFree(p->d_tc);
   if (p->d_rctw) cudaFree(p->d_rctw);
+  if (p->d_radtw) cudaFree(p->d_radtw);
   if (p->d_tables) cudaFree(p->d_tables);
   delete p;
 }
@@ -270,11 +271,12 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
   }
   TileArgs a;
   base_args(a);
-  const int C = p->k1->C;
+  const TileKernelInfo* k = p->kradix ? p->kradix : p->k1;
+  const int C = k->C;
   const long long L = p->n;
   a.in = in;
   a.out = out;
-  a.tw = p->tw1;
+  a.tw = p->kradix ? (const float2*)p->d_radtw : p->tw1;
   a.tiles_per_batch = (p->batch + C - 1) / C;
   a.in_gstride = a.out_gstride = (long long)C * L;
   a.in_sc = a.out_sc = L;
@@ -302,7 +304,7 @@ static int exec_single(fft_plan* p, const float2* in, float2* out, int dir, cuda
                ? FFT_OK
                : FFT_ERR_CUDA;
   }
-  return launch_tile(p->k1, a, a.tiles_per_batch, s);
+  return launch_tile(k, a, a.tiles_per_batch, s);
 }
 
 // Attach the tensor-TMA variant to every column pass that has one, when
@@ -649,6 +651,13 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   dflt.fused = -1;
   dflt.halves = 0;
   if (!cfg) cfg = &dflt;
+  // radix 4 / 8: one on-chip FP32 pass on the register path only, where a
+  // kernel is compiled (checked before any CUDA call)
+  const bool small_radix = cfg->radix > 0 && cfg->radix != 16;
+  if (small_radix && ((cfg->radix != 4 && cfg->radix != 8) || cfg->npass > 1 || cfg->tma > 0 || cfg->fused > 0 ||
+                      cfg->halves == 2 || p->prec != FFT_PREC_FP32 ||
+                      !tile_kernel_radix(lgN, cfg->radix == 8 ? 3 : 2)))
+    return FFT_ERR_UNSUPPORTED;
   // fused two-pass launch (fused.cu): only on request (config or
   // GBFFT_FUSED=1) or when the autotuner measures it faster.  Measured on
   // GB300 it keeps the intermediate in L2 (DRAM reads = input only) but loses
@@ -695,6 +704,21 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
             cudaStreamSynchronize(0) != cudaSuccess)
           return FFT_ERR_CUDA;
       }
+    }
+    // Radix-8 / radix-4 passes with 8 / 4 points per thread (autotuner
+    // option): more, lighter threads and more passes over shared memory.
+    if (small_radix) {
+      const int lgm = cfg->radix == 8 ? 3 : 2;
+      p->kradix = tile_kernel_radix(lgN, lgm);
+      rc = prepare_kernel(p->kradix);
+      if (rc) return rc;
+      p->radix_lgm = lgm;
+      const size_t nt = (size_t)stage_tw_size(lgN, false, lgm);
+      if (cudaMalloc(&p->d_radtw, nt * 8 + 8) != cudaSuccess) return FFT_ERR_ALLOC;
+      if (launch_gen_stage_twiddles((float2*)p->d_radtw, lgN, 0, false, lgm) != cudaSuccess ||
+          cudaStreamSynchronize(0) != cudaSuccess)
+        return FFT_ERR_CUDA;
+      return build_tables(p, lgN, 0, 0);
     }
     // Two CTAs per transform (radix-2 split) is an autotuner option: with the
     // linear shared-memory addressing the one-CTA pass measures faster at
@@ -1457,12 +1481,14 @@ int fft_plan_get_config(const fft_plan* p, fft_plan_config* out) {
   out->tma = -1;
   out->fused = 0;
   out->halves = 1;
+  out->radix = 16;
   if (p->kind == KIND_SINGLE) {
     out->npass = 1;
     out->lg1 = p->lg;
     out->c1 = p->c1;
     out->tma = p->ktma ? 1 : (p->kpfs ? 3 : (p->kpf ? 2 : 0));
     out->halves = p->kdif2 ? 2 : 1;
+    out->radix = p->kradix ? (1 << p->radix_lgm) : 16;
   } else if (p->kind == KIND_FOURSTEP) {
     out->npass = p->npass ? p->npass : 2;
     out->fused = p->fused ? 1 : 0;

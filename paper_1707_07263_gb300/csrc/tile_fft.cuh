@@ -44,30 +44,33 @@
 namespace gbfft {
 
 // ---------------------------------------------------------------------------
-// Radix schedule for L = 2^LG: the remainder pass first, then radix-16 passes
-// (rev = false, every kernel); or the radix-16 passes first and the remainder
-// pass last (rev = true: the second transform of the fused range-compression
-// kernel, whose first pass then needs exactly the points that the first
-// transform's last pass left in each thread).
+// Radix schedule for L = 2^LG with radices up to 2^lgm (lgm = 4, radix 16, for
+// every kernel but the smaller-radix single-pass variants the autotuner may
+// pick): the remainder pass first, then full-radix passes (rev = false); or
+// the full-radix passes first and the remainder pass last (rev = true: the
+// second transform of the fused range-compression kernel, whose first pass
+// then needs exactly the points that the first transform's last pass left in
+// each thread).
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr int radix_nst(int lg) { return (lg + 3) / 4; }
-__host__ __device__ constexpr int radix_lgr(int lg, int s, bool rev = false) {
-  return (lg % 4 != 0 && s == (rev ? radix_nst(lg) - 1 : 0)) ? (lg % 4) : 4;
+__host__ __device__ constexpr int radix_nst(int lg, int lgm = 4) { return (lg + lgm - 1) / lgm; }
+__host__ __device__ constexpr int radix_lgr(int lg, int s, bool rev = false, int lgm = 4) {
+  return (lg % lgm != 0 && s == (rev ? radix_nst(lg, lgm) - 1 : 0)) ? (lg % lgm) : lgm;
 }
-__host__ __device__ constexpr int radix_lgns(int lg, int s, bool rev = false) {
-  return s == 0 ? 0 : radix_lgns(lg, s - 1, rev) + radix_lgr(lg, s - 1, rev);
+__host__ __device__ constexpr int radix_lgns(int lg, int s, bool rev = false, int lgm = 4) {
+  return s == 0 ? 0 : radix_lgns(lg, s - 1, rev, lgm) + radix_lgr(lg, s - 1, rev, lgm);
 }
 // Offset (in complex entries) of pass s's twiddle basis in the per-length
 // table.  Pass s with Ns > 1 stores lgr(s) rows of Ns entries:
 //   row e (e = 0..lgr-1), column k:  W_{Ns*R}^{(2^e) * k}.
-__host__ __device__ constexpr int stage_tw_off(int lg, int s, bool rev = false) {
+__host__ __device__ constexpr int stage_tw_off(int lg, int s, bool rev = false, int lgm = 4) {
   return s == 0 ? 0
-                : stage_tw_off(lg, s - 1, rev) +
-                      ((radix_lgns(lg, s - 1, rev) > 0) ? radix_lgr(lg, s - 1, rev) * (1 << radix_lgns(lg, s - 1, rev))
-                                                        : 0);
+                : stage_tw_off(lg, s - 1, rev, lgm) +
+                      ((radix_lgns(lg, s - 1, rev, lgm) > 0)
+                           ? radix_lgr(lg, s - 1, rev, lgm) * (1 << radix_lgns(lg, s - 1, rev, lgm))
+                           : 0);
 }
-__host__ __device__ constexpr int stage_tw_size(int lg, bool rev = false) {
-  return stage_tw_off(lg, radix_nst(lg), rev);
+__host__ __device__ constexpr int stage_tw_size(int lg, bool rev = false, int lgm = 4) {
+  return stage_tw_off(lg, radix_nst(lg, lgm), rev, lgm);
 }
 
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
@@ -76,16 +79,19 @@ __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // Row pad (complex entries) so that the lane groups of one warp that touch
 // different transforms land on disjoint banks (derived from a bank model of
 // every pass's access pattern).
-__host__ __device__ constexpr int tile_group_count(int lg, int C, bool in_cf, bool out_cf, int s) {
-  return (s >= radix_nst(lg))
+__host__ __device__ constexpr int tile_group_count(int lg, int C, bool in_cf, bool out_cf, int s, int lgm = 4) {
+  return (s >= radix_nst(lg, lgm))
              ? 1
-             : cmax(cmin(C, (((s == 0) && in_cf) || ((s == radix_nst(lg) - 1) && out_cf))
+             : cmax(cmin(C, (((s == 0) && in_cf) || ((s == radix_nst(lg, lgm) - 1) && out_cf))
                                   ? cmin(C, 32)
-                                  : (((1 << lg) >> radix_lgr(lg, s)) < 32 ? cmax(1, 32 / ((1 << lg) >> radix_lgr(lg, s))) : 1)),
-                    tile_group_count(lg, C, in_cf, out_cf, s + 1));
+                                  : (((1 << lg) >> radix_lgr(lg, s, false, lgm)) < 32
+                                         ? cmax(1, 32 / ((1 << lg) >> radix_lgr(lg, s, false, lgm)))
+                                         : 1)),
+                    tile_group_count(lg, C, in_cf, out_cf, s + 1, lgm));
 }
-__host__ __device__ constexpr int tile_row_pad(int lg, int C, bool in_cf, bool out_cf) {
-  return ((32 / tile_group_count(lg, C, in_cf, out_cf, 0)) % 16 - (((1 << lg) + ((1 << lg) >> 4)) % 16) + 32) % 16;
+__host__ __device__ constexpr int tile_row_pad(int lg, int C, bool in_cf, bool out_cf, int lgm = 4) {
+  return ((32 / tile_group_count(lg, C, in_cf, out_cf, 0, lgm)) % 16 - (((1 << lg) + ((1 << lg) >> 4)) % 16) + 32) %
+         16;
 }
 
 // Shared-memory index of element n of a transform's row:
@@ -97,13 +103,16 @@ __host__ __device__ constexpr int tc_row_pad(int C, bool in_cf, bool out_cf) {
   return (in_cf || out_cf) ? (C == 2 ? 4 : 2) : 0;
 }
 
-template <int LG, int C, bool IN_CF, bool OUT_CF, int IDX = 0>
+// LGM: log2 of the largest radix, which is also the number of points each
+// thread holds (4: radix 16, every kernel but the autotuner's smaller-radix
+// single-pass variants, 3: radix 8, 2: radix 4).
+template <int LG, int C, bool IN_CF, bool OUT_CF, int IDX = 0, int LGM = 4>
 struct TileCfg {
   static constexpr int L = 1 << LG;
-  static constexpr int P = L < 16 ? L : 16;         // points per thread
-  static constexpr int T = C * L / P;               // threads per CTA
-  static constexpr int NST = radix_nst(LG);
-  static constexpr int LP = IDX == 0 ? L + (L >> 4) + tile_row_pad(LG, C, IN_CF, OUT_CF)
+  static constexpr int P = L < (1 << LGM) ? L : (1 << LGM);   // points per thread
+  static constexpr int T = C * L / P;                         // threads per CTA
+  static constexpr int NST = radix_nst(LG, LGM);
+  static constexpr int LP = IDX == 0 ? L + (L >> 4) + tile_row_pad(LG, C, IN_CF, OUT_CF, LGM)
                                      : L + tc_row_pad<IDX>(C, IN_CF, OUT_CF);
   static constexpr int SM_TILE = NST > 1 ? C * LP : 0;   // complex entries
   static constexpr bool EPI = IN_CF && OUT_CF;            // column pass: may carry the four-step twiddle
@@ -273,14 +282,14 @@ __device__ __forceinline__ void apply_stage_twiddle(float2* v, const float2* t, 
 //        PRE == 4, REV transform (radix-16 first pass: thread j reads n = j +
 //        r*L/16) without an exchange; lengths below 16 are one pass either way.
 template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int IDX = 0,
-          int POST = 0, bool REV = false>
-__device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
+          int POST = 0, bool REV = false, int LGM = 4>
+__device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF, 0, LGM>::P], float2* sm,
                                           const TileArgs& a, const float2* gin, float2* gout,
                                           long long col0, long long bidx, const float2* epi_tab) {
-  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF, IDX>;
+  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF, IDX, LGM>;
   constexpr int L = Cfg::L, P = Cfg::P, T = Cfg::T, NST = Cfg::NST, LP = Cfg::LP;
-  constexpr int LGR = radix_lgr(LG, S, REV), R = 1 << LGR;
-  constexpr int LGNS = radix_lgns(LG, S, REV), NS = 1 << LGNS;
+  constexpr int LGR = radix_lgr(LG, S, REV, LGM), R = 1 << LGR;
+  constexpr int LGNS = radix_lgns(LG, S, REV, LGM), NS = 1 << LGNS;
   constexpr bool FIRST = (S == 0), LAST = (S == NST - 1);
   constexpr bool CF = (FIRST && IN_CF) || (LAST && OUT_CF);
   constexpr int NB = P / R;   // butterflies per thread in this pass
@@ -424,7 +433,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
 
   // ---- twiddles W_{Ns*R}^{r*(j mod Ns)} ----
   if constexpr (NS > 1) {
-    const float2* t = (REV ? a.tw_rev : a.tw) + stage_tw_off(LG, S, REV);
+    const float2* t = (REV ? a.tw_rev : a.tw) + stage_tw_off(LG, S, REV, LGM);
 #pragma unroll
     for (int i = 0; i < NB; ++i) apply_stage_twiddle<R>(v + i * R, t, NS, jj[i] & (NS - 1));
   }
@@ -531,7 +540,7 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
       }
     }
   } else if constexpr (LAST) {
-    static_assert(NB == 1, "last pass is radix-16 (or the whole length)");
+    static_assert(NB == 1, "last pass is a full-radix pass (or the whole length)");
     // After the last pass NS = L/R and j < NS: output index k = j + q*NS.
     const int c = cc[0], j = jj[0];
     const bool ok = (col0 + c) < a.ncols;
@@ -597,21 +606,21 @@ __device__ __forceinline__ void tile_pass(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_
 }
 
 template <int LG, int C, bool IN_CF, bool OUT_CF, int S, bool OFFS = false, int PRE = 0, int POST = 0,
-          bool REV = false>
-__device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF>::P], float2* sm,
+          bool REV = false, int LGM = 4>
+__device__ __forceinline__ void tile_stage(float2 (&v)[TileCfg<LG, C, IN_CF, OUT_CF, 0, LGM>::P], float2* sm,
                                            const TileArgs& a, const float2* gin, float2* gout,
                                            long long col0, long long bidx, const float2* epi_tab) {
-  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS, PRE, 0, POST, REV>(v, sm, a, gin, gout, col0, bidx, epi_tab);
-  if constexpr (S + 1 < TileCfg<LG, C, IN_CF, OUT_CF>::NST)
-    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS, PRE, POST, REV>(v, sm, a, gin, gout, col0, bidx, epi_tab);
+  tile_pass<LG, C, IN_CF, OUT_CF, S, OFFS, PRE, 0, POST, REV, LGM>(v, sm, a, gin, gout, col0, bidx, epi_tab);
+  if constexpr (S + 1 < TileCfg<LG, C, IN_CF, OUT_CF, 0, LGM>::NST)
+    tile_stage<LG, C, IN_CF, OUT_CF, S + 1, OFFS, PRE, POST, REV, LGM>(v, sm, a, gin, gout, col0, bidx, epi_tab);
 }
 
 // One tile of a pass: tile index `tile` of the launch described by `a`, using
 // `smem` (TileCfg::SMEM_BYTES).  Shared by the one-tile-per-CTA kernel below
 // and the persistent uneven-batch kernel.
-template <int LG, int C, bool IN_CF, bool OUT_CF, bool OFFS = false, int PRE = 0, int POST = 0>
+template <int LG, int C, bool IN_CF, bool OUT_CF, bool OFFS = false, int PRE = 0, int POST = 0, int LGM = 4>
 __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, float2* smem) {
-  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF>;
+  using Cfg = TileCfg<LG, C, IN_CF, OUT_CF, 0, LGM>;
   float2* sm = smem;
   float2* epi_tab = smem + Cfg::SM_TILE;
 
@@ -628,7 +637,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, flo
 
   if (Cfg::EPI && a.ft_lgN) {
     // per-column step factors W_N^{n2*NS_last*q}, q = 0..15
-    constexpr int NS_LAST = 1 << radix_lgns(LG, Cfg::NST - 1);
+    constexpr int NS_LAST = 1 << radix_lgns(LG, Cfg::NST - 1, false, LGM);
     for (int e = threadIdx.x; e < C * 16; e += Cfg::T) {
       const int q = e / C, c = e - q * C;   // entry q*C + c
       const unsigned n2 = a.ft_by_batch ? (unsigned)b : (unsigned)(col0 + c);
@@ -641,7 +650,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, long long tile, flo
   }
 
   float2 v[Cfg::P];
-  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS, PRE, POST>(v, sm, a, gin, gout, col0, b, epi_tab);
+  tile_stage<LG, C, IN_CF, OUT_CF, 0, OFFS, PRE, POST, false, LGM>(v, sm, a, gin, gout, col0, b, epi_tab);
 }
 
 // Two CTAs per transform of length 2^(LG+1) (radix-2 decimation in
@@ -662,11 +671,14 @@ __global__ void __launch_bounds__(TileCfg<LG, 1, false, false>::T, (LG >= 13 ? 2
                                                k1, nullptr);
 }
 
-template <int LG, int C, bool IN_CF, bool OUT_CF>
-__global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF>::T)
+// LGM < 4: the same pass with radix-8 (LGM = 3) or radix-4 (LGM = 2) passes
+// and as many points per thread (single-pass variants the autotuner may pick;
+// stage table built for that schedule).
+template <int LG, int C, bool IN_CF, bool OUT_CF, int LGM = 4>
+__global__ void __launch_bounds__(TileCfg<LG, C, IN_CF, OUT_CF, 0, LGM>::T)
     tile_fft_kernel(const TileArgs a) {
   extern __shared__ float2 smem[];
-  tile_body<LG, C, IN_CF, OUT_CF>(a, (long long)blockIdx.x, smem);
+  tile_body<LG, C, IN_CF, OUT_CF, false, 0, 0, LGM>(a, (long long)blockIdx.x, smem);
 }
 
 // Persistent single-pass variant for one transform per CTA (C == 1, contiguous

@@ -40,6 +40,11 @@ const TileKernelInfo* tile_kernel_rowtmas(int lg, int C);
 bool rowtmas_usable(const TileKernelInfo* k, const TileArgs& a, const void* out, long long ntiles);
 int rowtmas_launch(const TileKernelInfo* k, const TileArgs& a, long long ntiles, cudaStream_t s);
 
+// MAP_JJ single-pass variants with radix-8 (lgm = 3, 2^5..2^13) or radix-4
+// (lgm = 2, 2^5..2^12) passes and as many points per thread, jj_cols(lg)
+// transforms per CTA; NULL where not compiled.
+const TileKernelInfo* tile_kernel_radix(int lg, int lgm);
+
 // Two-CTA radix-2 split kernels (tile_fft_dif2_kernel) for half length 2^lg.
 const TileKernelInfo* tile_kernel_dif2(int lg);
 

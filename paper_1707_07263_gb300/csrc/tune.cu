@@ -1,8 +1,9 @@
 // tune.cu -- the autotuner: time candidate plan configurations on the caller's
 // buffers and keep the fastest.  The paper fixes its partition thresholds by
 // hand for the C2070 (Sec. 2.3.2, Sec. 3); here the split, the number of
-// passes, the columns per CTA and the staging kernel are measured per shape
-// on the GPU at hand.
+// passes, the columns per CTA, the staging kernel and, for one on-chip pass,
+// the largest radix (with it the points per thread and the threads per CTA)
+// are measured per shape on the GPU at hand.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -59,6 +60,13 @@ static std::vector<fft_plan_config> candidates(int lgN) {
     c.tma = 0;
     c.halves = 2;  // rejected where no split kernel exists
     v.push_back(c);
+    c.halves = 0;
+    // largest radix 8 or 4 (as many points per thread, so 2x / 4x the
+    // threads per CTA); rejected where not compiled
+    for (int r = 4; r <= 8; r *= 2) {
+      c.radix = r;
+      v.push_back(c);
+    }
   }
   if (lgN >= 10) {
     for (int lg1 = lgN / 2 - 2; lg1 <= (lgN + 1) / 2 + 2; ++lg1) {

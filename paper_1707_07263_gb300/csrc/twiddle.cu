@@ -20,15 +20,15 @@ __device__ __forceinline__ float2 w_entry(long long m, long long M) {
 }
 
 // Stage table of length L = 2^lg: for pass s with Ns > 1, row e, column k
-// holds W_{Ns*R}^{2^e * k} at stage_tw_off(lg, s, rev) + e*Ns + k (rev: the
-// remainder-last schedule).
-__global__ void gen_stage_twiddles(float2* tab, int lg, bool rev) {
-  const int total = stage_tw_size(lg, rev);
+// holds W_{Ns*R}^{2^e * k} at stage_tw_off(lg, s, rev, lgm) + e*Ns + k (rev:
+// the remainder-last schedule; lgm: log2 of the largest radix).
+__global__ void gen_stage_twiddles(float2* tab, int lg, bool rev, int lgm) {
+  const int total = stage_tw_size(lg, rev, lgm);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     int s = 1;
-    while (s + 1 < radix_nst(lg) && idx >= stage_tw_off(lg, s + 1, rev)) ++s;
-    const int local = idx - stage_tw_off(lg, s, rev);
-    const int lgns = radix_lgns(lg, s, rev), lgr = radix_lgr(lg, s, rev);
+    while (s + 1 < radix_nst(lg, lgm) && idx >= stage_tw_off(lg, s + 1, rev, lgm)) ++s;
+    const int local = idx - stage_tw_off(lg, s, rev, lgm);
+    const int lgns = radix_lgns(lg, s, rev, lgm), lgr = radix_lgr(lg, s, rev, lgm);
     const int NS = 1 << lgns;
     const int e = local / NS, k = local % NS;
     const long long M = 1LL << (lgns + lgr);
@@ -104,12 +104,12 @@ cudaError_t launch_gen_twiddles_step(void* tab, bool fp64, long long N, long lon
   return cudaGetLastError();
 }
 
-cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev) {
-  const int total = stage_tw_size(lg, rev);
+cudaError_t launch_gen_stage_twiddles(float2* tab, int lg, cudaStream_t s, bool rev, int lgm) {
+  const int total = stage_tw_size(lg, rev, lgm);
   if (total == 0) return cudaSuccess;
   const int threads = 256;
   const int blocks = (total + threads - 1) / threads;
-  gen_stage_twiddles<<<blocks, threads, 0, s>>>(tab, lg, rev);
+  gen_stage_twiddles<<<blocks, threads, 0, s>>>(tab, lg, rev, lgm);
   return cudaGetLastError();
 }
 

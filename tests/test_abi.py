@@ -72,6 +72,33 @@ def test_mixed_radix_tensor_core_is_unsupported(lib):
     assert lib.fft_last_error() == -6
 
 
+@pytest.mark.parametrize("n,cfg", [
+    (1 << 10, {"radix": 2}),
+    (1 << 10, {"radix": 32}),
+    (1 << 10, {"radix": 12}),
+    (1 << 14, {"radix": 8}),               # 2048 threads: not compiled
+    (1 << 13, {"radix": 4}),
+    (1 << 4, {"radix": 8}),                # below the compiled range
+    (1 << 15, {"radix": 8}),               # multi-pass length
+    (1 << 12, {"radix": 8, "npass": 2}),
+    (1 << 12, {"radix": 4, "tma": 1}),
+    (1 << 12, {"radix": 8, "tma": 3}),
+    (1 << 12, {"radix": 8, "halves": 2}),
+    (1 << 12, {"radix": 4, "fused": 1}),
+])
+def test_plan_config_radix_without_kernel_is_unsupported(lib, n, cfg):
+    """A largest radix other than 16 exists only for one on-chip FP32 pass on
+    the register path (radix 8: 2^5..2^13, radix 4: 2^5..2^12); everything
+    else is refused before any launch or allocation."""
+    from paper_1707_07263_gb300 import _lib
+    c = _lib.FftPlanConfig.from_dict(cfg)
+    assert lib.fft_plan_create_config(n, 1, 0, 0, ctypes.byref(c)) is None, cfg
+    assert lib.fft_last_error() == -6
+    c = _lib.FftPlanConfig.from_dict({"radix": 8})
+    assert lib.fft_plan_create_config(1 << 10, 1, 0, 1, ctypes.byref(c)) is None   # tensor-core precision
+    assert lib.fft_last_error() == -6
+
+
 def test_plan_create_2d_rejects(lib):
     assert lib.fft_plan_create_2d(11, 16, 1, 0, 0) is None    # prime side
     assert lib.fft_plan_create_2d(16, 26, 1, 0, 0) is None    # side with factor 13

@@ -174,3 +174,60 @@ def test_staged_persistent_kernel_loops(lib, lg, d):
     assert oracle.rel_l2_rows(got, ref).max() <= 5e-7 * lg
     got8 = out8.cpu().numpy().reshape(batch, n)
     assert oracle.rel_l2_rows(got8, ref).max() <= 5e-7 * lg
+
+
+RADIX_CASES = [(8, lg) for lg in range(5, 14)] + [(4, lg) for lg in range(5, 13)]
+
+
+@pytest.mark.parametrize("radix,lg", RADIX_CASES)
+def test_smaller_radix_single_pass(lib, radix, lg):
+    """One on-chip pass with radix-8 or radix-4 Stockham passes (8 / 4 points
+    per thread, so 2x / 4x the threads of the radix-16 kernel): every compiled
+    length, a batch of two full tiles plus a ragged one, every direction
+    through one plan, and one call in place; each transform against the
+    oracle.  The plan reports the radix it was built with."""
+    n = 1 << lg
+    cols = (4096 >> lg) if lg < 12 else 1
+    batch = 2 * cols + max(1, cols // 3)
+    x = workloads.cgauss(n, batch, seed=8700 + 16 * lg + radix)
+    c = _lib.FftPlanConfig.from_dict({"npass": 1, "tma": 0, "radix": radix})
+    h = ctypes.c_void_p(lib.fft_plan_create_config(n, batch, 0, 0, ctypes.byref(c)))
+    assert h.value, _lib.ERRORS.get(lib.fft_last_error())
+    got_cfg = _lib.FftPlanConfig()
+    assert lib.fft_plan_get_config(h, ctypes.byref(got_cfg)) == 0
+    assert got_cfg.radix == radix and got_cfg.npass == 1 and got_cfg.tma == 0
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    xt = torch.from_numpy(x).cuda()
+    x64 = x.astype(np.complex128)
+    refs = {0: oracle.fft(x64), 1: oracle.fft(x64, oracle.INVERSE), 2: oracle.fft(x64, oracle.ADJOINT),
+            3: oracle.fft(x64) / n}
+    for d in range(4):
+        out = torch.empty_like(xt)
+        assert lib.fft_exec_dir(h, ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(out.data_ptr()), d, s) == 0
+        torch.cuda.synchronize()
+        err = oracle.rel_l2_rows(out.cpu().numpy(), refs[d]).max()
+        assert err <= 5e-7 * lg, (radix, lg, d, err)
+    y = xt.clone()
+    assert lib.fft_exec_dir(h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(y.data_ptr()), 1, s) == 0
+    torch.cuda.synchronize()
+    assert oracle.rel_l2_rows(y.cpu().numpy(), refs[1]).max() <= 5e-7 * lg
+    lib.fft_destroy(h)
+
+
+@pytest.mark.parametrize("lg", [9, 12])
+def test_smaller_radix_agrees_with_radix16(lib, lg):
+    """The three schedules compute the same transform: outputs of the radix-4,
+    radix-8 and radix-16 single passes agree with each other to the FP32
+    bound on a larger batch (many CTAs)."""
+    n = 1 << lg
+    batch = (1 << 20) // n + 7
+    x = workloads.cgauss(n, batch, seed=8800 + lg)
+    outs = {}
+    for r in (16, 8, 4):
+        got, used = run_cfg(lib, x, {"npass": 1, "tma": 0, "radix": r})
+        assert used["radix"] == r
+        outs[r] = got.reshape(batch, n).astype(np.complex128)
+    ref = oracle.fft(x.astype(np.complex128)[:64])
+    for r in (16, 8, 4):
+        assert oracle.rel_l2_rows(outs[r][:64], ref).max() <= 5e-7 * lg
+        assert oracle.rel_l2_rows(outs[r], outs[16]).max() <= 1e-6 * lg

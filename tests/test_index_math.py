@@ -4,7 +4,9 @@
    Stockham passes splits as pidx(base + d) = pidx(base) + pidx(d) for every
    butterfly's element offsets (reads d = r L/R from base j, writes d = q Ns
    from base (j div Ns) Ns R + (j mod Ns)), in the forward radix schedule
-   (remainder pass first) and the reversed one (remainder last).  The kernels
+   (remainder pass first) and the reversed one (remainder last), with radix-16
+   passes and with the radix-8 and radix-4 passes of the autotuner's
+   smaller-radix single-pass variants.  The kernels
    address each butterfly's elements as one base register plus constants on
    the strength of it.
 2. The mixed-radix kernel divides by run-time d with q = floor(n m / 2^32),
@@ -22,28 +24,29 @@ def pidx(n):
     return n + (n >> 4)
 
 
-def schedule(lg: int, rev: bool):
-    """log2 of the radices, pass by pass: 16s plus one 2/4/8 remainder."""
-    rest = [4] * (lg // 4)
-    if lg % 4:
-        rest = rest + [lg % 4] if rev else [lg % 4] + rest
+def schedule(lg: int, rev: bool, lgm: int = 4):
+    """log2 of the radices, pass by pass: full radix-2^lgm passes plus one
+    smaller remainder pass (first, or last when rev)."""
+    rest = [lgm] * (lg // lgm)
+    if lg % lgm:
+        rest = rest + [lg % lgm] if rev else [lg % lgm] + rest
     return rest
 
 
-@pytest.mark.parametrize("rev", [False, True])
+@pytest.mark.parametrize("rev,lgm", [(False, 4), (True, 4), (False, 3), (False, 2)])
 @pytest.mark.parametrize("lg", range(1, 15))
-def test_padded_index_splits(lg, rev):
+def test_padded_index_splits(lg, rev, lgm):
     L = 1 << lg
     lgns = 0
-    for lgr in schedule(lg, rev):
+    for lgr in schedule(lg, rev, lgm):
         R, Ns = 1 << lgr, 1 << lgns
         j = np.arange(L // R)
         r = np.arange(R)[:, None]
         d_read = r * (L // R)
-        assert np.array_equal(pidx(j + d_read), pidx(j) + pidx(d_read)), ("read", lg, rev, R, Ns)
+        assert np.array_equal(pidx(j + d_read), pidx(j) + pidx(d_read)), ("read", lg, rev, lgm, R, Ns)
         base = (j // Ns) * Ns * R + (j % Ns)
         d_write = r * Ns
-        assert np.array_equal(pidx(base + d_write), pidx(base) + pidx(d_write)), ("write", lg, rev, R, Ns)
+        assert np.array_equal(pidx(base + d_write), pidx(base) + pidx(d_write)), ("write", lg, rev, lgm, R, Ns)
         lgns += lgr
     assert lgns == lg
 

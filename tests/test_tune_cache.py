@@ -39,6 +39,7 @@ def test_shipped_entries_are_well_formed():
         assert sorted(c) == sorted(fields), k
         assert v["us"] > 0
         assert c["tma"] in (-1, 0, 1, 2, 3) and c["fused"] in (-1, 0, 1) and c["halves"] in (0, 1, 2)
+        assert c["radix"] == 16 or (c["radix"] in (4, 8) and c["npass"] == 1 and c["tma"] == 0), k
         if c["npass"] == 1:
             assert c["lg1"] == lg <= 14, k
         elif c["npass"] == 2:
