@@ -652,11 +652,16 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
   dflt.halves = 0;
   if (!cfg) cfg = &dflt;
   // radix 4 / 8: one on-chip FP32 pass on the register path only, where a
-  // kernel is compiled (checked before any CUDA call)
-  const bool small_radix = cfg->radix > 0 && cfg->radix != 16;
-  if (small_radix && ((cfg->radix != 4 && cfg->radix != 8) || cfg->npass > 1 || cfg->tma > 0 || cfg->fused > 0 ||
-                      cfg->halves == 2 || p->prec != FFT_PREC_FP32 ||
-                      !tile_kernel_radix(lgN, cfg->radix == 8 ? 3 : 2)))
+  // kernel is compiled (checked before any CUDA call).  Left open by the
+  // configuration, the planner takes radix-8 passes at 2^5 and 2^6, where
+  // they measured faster on GB300 than radix 16 (per 2^26 points: 2^5 224 ->
+  // 176 us, 2^6 162 -> 158 us; bench.py --workload radix).
+  const bool open_kernel = cfg->radix <= 0 && cfg->npass <= 1 && cfg->tma < 0 && cfg->fused <= 0 &&
+                           cfg->halves != 2 && p->prec == FFT_PREC_FP32;
+  const int radix = cfg->radix > 0 ? cfg->radix : ((open_kernel && (lgN == 5 || lgN == 6)) ? 8 : 16);
+  const bool small_radix = radix != 16;
+  if (small_radix && ((radix != 4 && radix != 8) || cfg->npass > 1 || cfg->tma > 0 || cfg->fused > 0 ||
+                      cfg->halves == 2 || p->prec != FFT_PREC_FP32 || !tile_kernel_radix(lgN, radix == 8 ? 3 : 2)))
     return FFT_ERR_UNSUPPORTED;
   // fused two-pass launch (fused.cu): only on request (config or
   // GBFFT_FUSED=1) or when the autotuner measures it faster.  Measured on
@@ -708,7 +713,7 @@ static int plan_1d(fft_plan* p, int lgN, const fft_plan_config* cfg) {
     // Radix-8 / radix-4 passes with 8 / 4 points per thread (autotuner
     // option): more, lighter threads and more passes over shared memory.
     if (small_radix) {
-      const int lgm = cfg->radix == 8 ? 3 : 2;
+      const int lgm = radix == 8 ? 3 : 2;
       p->kradix = tile_kernel_radix(lgN, lgm);
       rc = prepare_kernel(p->kradix);
       if (rc) return rc;
@@ -1695,12 +1700,14 @@ int fft_plan_kind(const fft_plan* plan) { return is_live(plan) ? plan->kind : -1
 int fft_plan_describe(const fft_plan* p, char* buf, size_t len) {
   if (!is_live(p) || !buf || len == 0) return set_err(FFT_ERR_INVALID_ARG);
   static const char* kinds[] = {"single", "fourstep", "2d", "many", "real", "mixed", "mixed_passes", "?"};
+  const TileKernelInfo* k1 = p->kradix ? p->kradix : p->k1;   // the first kernel that runs
   snprintf(buf, len,
            "kind=%s n=%lld batch=%lld lg1=%d lg2=%d c1=%d c2=%d threads1=%d smem1=%d threads2=%d smem2=%d "
-           "prec=%d launches=%d ws=%zu tma_grid=%lld",
+           "prec=%d launches=%d ws=%zu tma_grid=%lld radix=%d",
            kinds[p->kind & 7], (long long)p->n, (long long)p->batch, p->lg1, p->lg2, p->c1, p->c2,
-           p->k1 ? p->k1->threads : 0, p->k1 ? p->k1->smem_bytes : 0, p->k2 ? p->k2->threads : 0,
-           p->k2 ? p->k2->smem_bytes : 0, p->prec, p->launches, p->ws_bytes, p->ktma ? p->tma_grid : 0LL);
+           k1 ? k1->threads : 0, k1 ? k1->smem_bytes : 0, p->k2 ? p->k2->threads : 0,
+           p->k2 ? p->k2->smem_bytes : 0, p->prec, p->launches, p->ws_bytes, p->ktma ? p->tma_grid : 0LL,
+           p->kradix ? 1 << p->radix_lgm : 16);
   return FFT_OK;
 }
 

@@ -231,3 +231,27 @@ def test_smaller_radix_agrees_with_radix16(lib, lg):
     for r in (16, 8, 4):
         assert oracle.rel_l2_rows(outs[r][:64], ref).max() <= 5e-7 * lg
         assert oracle.rel_l2_rows(outs[r], outs[16]).max() <= 1e-6 * lg
+
+
+@pytest.mark.parametrize("lg,radix", [(4, 16), (5, 8), (6, 8), (7, 16), (12, 16)])
+def test_planner_default_radix(lib, lg, radix):
+    """Left open by the configuration, one on-chip FP32 pass takes radix-8
+    passes at 2^5 and 2^6 (measured faster there) and radix 16 elsewhere; the
+    plan's description reports it, and the result matches the oracle."""
+    n = 1 << lg
+    batch = 77
+    h = ctypes.c_void_p(lib.fft_plan_create(n, batch, 0, 0))
+    assert h.value
+    c = _lib.FftPlanConfig()
+    assert lib.fft_plan_get_config(h, ctypes.byref(c)) == 0 and c.radix == radix
+    buf = ctypes.create_string_buffer(512)
+    lib.fft_plan_describe(h, buf, 512)
+    assert f"radix={radix}" in buf.value.decode()
+    x = workloads.cgauss(n, batch, seed=8900 + lg)
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    assert lib.fft_exec(h, ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    torch.cuda.synchronize()
+    lib.fft_destroy(h)
+    assert oracle.rel_l2_rows(out.cpu().numpy(), oracle.fft(x.astype(np.complex128))).max() <= 5e-7 * max(lg, 1)
