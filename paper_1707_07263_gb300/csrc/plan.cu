@@ -639,8 +639,9 @@ int exec_plan(fft_plan* p, const void* in, void* out, int dir, cudaStream_t s) {
 }
 
 // Planner for 1-D lengths: kind, split and kernel variants.  cfg fields <= 0
-// (or tma < 0) take the defaults: one on-chip pass up to 2^14 (TMA-staged for
-// 2^9..2^11, persistent with an L2 prefetch at 2^14), two passes
+// (or tma < 0) take the defaults: one on-chip pass up to 2^14 (radix-8 passes
+// at 2^5 and 2^6, TMA-staged for 2^9..2^11, persistent with the next transform
+// staged into the exchange buffer at 2^13 and 2^14), two passes
 // below 2^22 (2^8-point column tiles from 2^16 to 2^20, else the even split),
 // three passes 2^8 * 2^8 * rest from 2^22; as many adjacent columns per CTA
 // as fit 2^13 points (at most 16).
