@@ -286,8 +286,10 @@ GBFFT_API int fft_pointer_usable(const void* ptr, size_t bytes);
  * radix of the Stockham passes, which is also the number of points each
  * thread holds, and so sets the threads per CTA (transforms per CTA x n /
  * radix): 8 = radix-8 passes (n = 2^5..2^13), 4 = radix-4 passes
- * (n = 2^5..2^12), 16 or <= 0 = radix-16 passes (the default; every other
- * kernel); any other value, or 4 / 8 where no such kernel is compiled, gives
+ * (n = 2^5..2^12), 16 = radix-16 passes (every other kernel), <= 0 = the
+ * planner's choice (radix 8 at n = 2^5 and 2^6 when npass, tma, fused and
+ * halves are left at their defaults too, radix 16 otherwise); any other
+ * value, or 4 / 8 where no such kernel is compiled, gives
  * FFT_ERR_UNSUPPORTED.  fft_plan_get_config reports 16 unless a smaller radix
  * was chosen.  These are the knobs of the autotuner (fft_autotune). */
 typedef struct fft_plan_config {
